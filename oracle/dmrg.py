@@ -1,0 +1,356 @@
+"""Plain two-site DMRG in FP64 on the CPU (test infrastructure only).
+
+Follows the two-site sweep algorithm of the paper (Sec. 2.1.2: the renormalized
+wavefunction lives on the product of the left block states, the d = 16 two-site local
+space and the right block states), with the standard Davidson solver (Sec. 2.1.3 (iv)
+names it; settings thrds = 1e-10 on the squared residual and dav_max_iter = 30 as in
+Listing 1), density-matrix truncation to M states per bond, and environments
+(renormalized operators) built from an MPO (Sec. 3.2).
+
+Representation (deliberately simple): every bond index runs over all its states in
+sector order, tensors are dense numpy arrays whose forbidden (quantum-number violating)
+entries are zero, and a label array gives (N, 2Sz) of each state.  Truncation works per
+quantum-number sector, so the zeros stay exact zeros.
+
+Index conventions
+  A[k]      (M_k, 4, M_{k+1}) site tensor, bond k between sites k-1 and k
+  L[k][w]   (M_k, M_k) left environment of channel w on bond k: <l'| left part of w |l>
+  R[k][w]   (M_k, M_k) right environment of channel w on bond k (right block states are
+            labelled by bond k's left-block quantum numbers)
+  psi       (M_i, 4, 4, M_{i+2}) two-site wavefunction of window (i, i+1)
+Operator ordering on |l s1 s2 r> is (left part)(site i)(site i+1)(right part); moving an
+odd operator past an odd number of fermions costs a sign (Sec. "Fermion convention" of
+``mpo``).
+"""
+import numpy as np
+
+from . import ops
+
+SITE_Q = np.array(ops.SITE_Q)
+
+
+# ----------------------------------------------------------------------------- layout
+def blocks_to_dense(bonds, sites):
+    """Block-sparse MPS (the ``synth`` file format) -> (labels, dense site tensors)."""
+    labels = []
+    for b in bonds:
+        lab = [(N, tsz) for (N, tsz, m) in b for _ in range(m)]
+        labels.append(np.array(lab, dtype=np.int64).reshape(-1, 2))
+    offs = [np.cumsum([0] + [m for (_, _, m) in b]) for b in bonds]
+    A = []
+    for k, blocks in enumerate(sites):
+        t = np.zeros((len(labels[k]), 4, len(labels[k + 1])))
+        for (jl, s, jr), blk in blocks.items():
+            t[offs[k][jl]:offs[k][jl + 1], s, offs[k + 1][jr]:offs[k + 1][jr + 1]] = blk
+        A.append(t)
+    return labels, A
+
+
+def parity_of(labels):
+    """(-1)^N for every state of a bond."""
+    return np.where(labels[:, 0] % 2 == 1, -1.0, 1.0)
+
+
+# ------------------------------------------------------------------------ environments
+def left_boundary():
+    return [np.ones((1, 1))]
+
+
+def right_boundary():
+    return [np.ones((1, 1))]
+
+
+def left_env_update(Lk, A, Wk, lab_k, n_chan_next):
+    """L_{k+1}[w'] = sum_{w,s',s} W_k[w,w']_{s's} (-1)^{p(op) n(l)} A_{s'}^T L_k[w] A_s."""
+    par = parity_of(lab_k)
+    out = [np.zeros((A.shape[2], A.shape[2])) for _ in range(n_chan_next)]
+    for (w, w2), m in Wk.items():
+        if Lk[w] is None:
+            continue
+        for s2, s in zip(*np.nonzero(m)):
+            odd = (ops.SITE_N[s2] + ops.SITE_N[s]) % 2
+            Lw = Lk[w] * par[None, :] if odd else Lk[w]
+            out[w2] += m[s2, s] * (A[:, s2, :].T @ Lw @ A[:, s, :])
+    return out
+
+
+def right_env_update(Rk1, B, Wk, parity_next, n_chan):
+    """R_k[w] = sum_{w',s',s} W_k[w,w']_{s's} (-1)^{p(w') n(s)} B_{s'} R_{k+1}[w'] B_s^T."""
+    out = [np.zeros((B.shape[0], B.shape[0])) for _ in range(n_chan)]
+    for (w, w2), m in Wk.items():
+        if Rk1[w2] is None:
+            continue
+        for s2, s in zip(*np.nonzero(m)):
+            sign = -1.0 if (parity_next[w2] and ops.SITE_N[s] % 2) else 1.0
+            out[w] += (sign * m[s2, s]) * (B[:, s2, :] @ Rk1[w2] @ B[:, s, :].T)
+    return out
+
+
+# ----------------------------------------------------------------- effective Hamiltonian
+def two_site_operators(mpo, i):
+    """{(a, b): O_ab} for window (i, i+1): O_ab = sum_w' W_i[a,w'] (x) W_{i+1}[w',b] as a
+    16 x 16 matrix over (s1, s2) = 4*s1 + s2, including the sign (-1)^{p(op2) n(s1)} of
+    moving the site-(i+1) operator past the site-i ket."""
+    right = {}
+    for (w2, b), m2 in mpo.W[i + 1].items():
+        right.setdefault(w2, []).append((b, m2))
+    out = {}
+    for (a, w2), m1 in mpo.W[i].items():
+        for b, m2 in right.get(w2, ()):
+            p2 = ops.op_parity(m2)
+            o = np.kron(m1 @ ops.PARITY if p2 else m1, m2)
+            out[(a, b)] = out.get((a, b), 0.0) + o
+    return {k: v for k, v in out.items() if np.any(v)}
+
+
+class Heff:
+    """H_eff of window (i, i+1) from L_i, R_{i+2} and the MPO (Sec. 2.1.2, Sec. 3.2).
+
+    Applied to psi: Y = sum_{a,b} (L_a P^{p(a)}) (x) O'_ab (x) R_b, where P is the parity of
+    the left ket and O'_ab = O_ab diag((-1)^{p(b) (n(s1) + n(s2))}) carries the sign of
+    moving the right part past the two site kets."""
+
+    def __init__(self, mpo, i, L, R, lab_l):
+        self.terms = two_site_operators(mpo, i)
+        self.L, self.R = L, R
+        self.par_l = parity_of(lab_l)
+        self.pa = mpo.parity[i]
+        self.pb = mpo.parity[i + 2]
+        n_in = np.add.outer(ops.SITE_N, ops.SITE_N).ravel()
+        self.sgn_in = np.where(n_in % 2 == 1, -1.0, 1.0)
+        by_a = {}
+        for (a, b), o in self.terms.items():
+            o2 = o * self.sgn_in[None, :] if self.pb[b] else o
+            by_a.setdefault(a, []).append((b, o2))
+        # per left channel a: the signed left operator, the stacked O'_ab and R_b^T
+        self.groups = []
+        for a, lst in by_a.items():
+            La = self.L[a] * self.par_l[None, :] if self.pa[a] else self.L[a]
+            Os = np.array([o for _, o in lst])                        # (nb, 16, 16)
+            RsT = np.array([self.R[b].T for b, _ in lst])             # (nb, mr, mr')
+            self.groups.append((La, Os, RsT))
+
+    def apply(self, psi):
+        ml, mr = psi.shape[0], psi.shape[3]
+        x = psi.reshape(ml, 16 * mr)
+        y = np.zeros((ml, 16, mr))
+        for La, Os, RsT in self.groups:
+            t = (La @ x).reshape(ml, 16, mr)
+            u = np.matmul(t[None], RsT[:, None])                     # (nb, ml, 16, mr')
+            # y[x, u, y'] += sum_{b, v} O'_b[u, v] u[b, x, v, y']
+            y += np.tensordot(Os, u, axes=([0, 2], [0, 2])).transpose(1, 0, 2)
+        return y.reshape(psi.shape)
+
+    def diag(self):
+        ml = self.L[0].shape[0]
+        mr = self.R[0].shape[0]
+        d = np.zeros((ml, 16, mr))
+        for (a, b), o in self.terms.items():
+            dl = np.diag(self.L[a]) * (self.par_l if self.pa[a] else 1.0)
+            dr = np.diag(self.R[b])
+            do = np.diag(o) * (self.sgn_in if self.pb[b] else 1.0)
+            d += dl[:, None, None] * do[None, :, None] * dr[None, None, :]
+        return d.reshape(ml, 4, 4, mr)
+
+
+# ------------------------------------------------------------------------------ Davidson
+def davidson(matvec, diag, x0, tol=1e-10, max_iter=30, max_sub=30):
+    """Lowest eigenpair by the standard Davidson method (Davidson 1975).
+
+    Subspace V (orthonormal) and W = H V; Rayleigh-Ritz on G = V^T W; residual
+    r = W s - theta V s; stop when |r|^2 <= tol or after max_iter products with H;
+    correction t = r / (D - theta) (denominators below 1e-8 in size set to 1e-8),
+    orthogonalised twice against V; a full subspace restarts from the Ritz vector.
+    Returns (theta, unit vector, number of products, |r|^2)."""
+    shape = x0.shape
+    d = diag.ravel()
+    v = x0.ravel() / np.linalg.norm(x0)
+    V = [v]
+    Wl = [matvec(v.reshape(shape)).ravel()]
+    nmv = 1
+    while True:
+        Vm, Wm = np.array(V).T, np.array(Wl).T
+        G = Vm.T @ Wm
+        G = 0.5 * (G + G.T)
+        evals, evecs = np.linalg.eigh(G)
+        theta, s = float(evals[0]), evecs[:, 0]
+        u, hu = Vm @ s, Wm @ s
+        r = hu - theta * u
+        rn2 = float(r @ r)
+        if rn2 <= tol or nmv >= max_iter:
+            break
+        den = d - theta
+        den = np.where(np.abs(den) < 1e-8, 1e-8, den)
+        t = r / den
+        if len(V) >= max_sub:
+            V, Wl = [u], [hu]
+        for _ in range(2):
+            for vv in V:
+                t = t - (vv @ t) * vv
+        tn = np.linalg.norm(t)
+        if tn < 1e-14:
+            break
+        t = t / tn
+        V.append(t)
+        Wl.append(matvec(t.reshape(shape)).ravel())
+        nmv += 1
+    u = u / np.linalg.norm(u)
+    return theta, u.reshape(shape), nmv, rn2
+
+
+# ---------------------------------------------------------------------------- truncation
+def _select(evals_by_sector, M, cutoff):
+    """Keep the M largest eigenvalues over all sectors.  Eigenvalues <= cutoff * max are
+    dropped.  Ties (|difference| <= 1e-14 * max) are broken by (sector index, index in
+    sector), both ascending.  Returns the kept count per sector."""
+    cand = []
+    for j, w in enumerate(evals_by_sector):
+        for t, lam in enumerate(w):
+            cand.append((float(lam), j, t))
+    if not cand:
+        return [0] * len(evals_by_sector)
+    lmax = max(c[0] for c in cand)
+    cand.sort(key=lambda c: -c[0])
+    # chain near-equal neighbours into groups, then order each group by (sector, index)
+    ordered, group = [], [cand[0]]
+    for c in cand[1:]:
+        if group[-1][0] - c[0] <= 1e-14 * lmax:
+            group.append(c)
+        else:
+            ordered.extend(sorted(group, key=lambda g: (g[1], g[2])))
+            group = [c]
+    ordered.extend(sorted(group, key=lambda g: (g[1], g[2])))
+    kept = [0] * len(evals_by_sector)
+    for lam, j, t in ordered[:M]:
+        if lam > cutoff * lmax:
+            kept[j] += 1
+    return kept
+
+
+def _sector_eigs(X, labels):
+    """Per sector q (sorted): eigenvalues (descending) and eigenvectors of X_q X_q^T,
+    X_q the rows of X labelled q."""
+    secs = sorted({tuple(q) for q in labels})
+    out = []
+    for q in secs:
+        rows = np.nonzero((labels[:, 0] == q[0]) & (labels[:, 1] == q[1]))[0]
+        xq = X[rows]
+        w, u = np.linalg.eigh(xq @ xq.T)
+        out.append((q, rows, w[::-1], u[:, ::-1]))
+    return out
+
+
+def left_split(psi, lab_l, M, cutoff=1e-14):
+    """psi (l s1, s2 r) -> A (l, s1, new) with A^T A = 1, C = A^T psi, new bond labels,
+    discarded weight."""
+    ml, _, _, mr = psi.shape
+    X = psi.reshape(ml * 4, 4 * mr)
+    row_lab = (lab_l[:, None, :] + SITE_Q[None, :, :]).reshape(-1, 2)
+    eig = _sector_eigs(X, row_lab)
+    kept = _select([e[2] for e in eig], M, cutoff)
+    cols, lab = [], []
+    for (q, rows, w, u), kq in zip(eig, kept):
+        for t in range(kq):
+            c = np.zeros(ml * 4)
+            c[rows] = u[:, t]
+            cols.append(c)
+            lab.append(q)
+    A = np.array(cols).T.reshape(ml, 4, len(cols))
+    C = (A.reshape(ml * 4, -1).T @ X).reshape(-1, 4, mr)
+    total = sum(float(np.sum(e[2])) for e in eig)
+    keptw = sum(float(np.sum(e[2][:kq])) for e, kq in zip(eig, kept))
+    return A, C, np.array(lab, dtype=np.int64).reshape(-1, 2), total - keptw
+
+
+def right_split(psi, lab_r, M, cutoff=1e-14):
+    """psi (l s1, s2 r) -> B (new, s2, r) with B B^T = 1, C = psi B^T, new bond labels
+    (left-block quantum numbers of the new bond), discarded weight."""
+    ml, _, _, mr = psi.shape
+    X = psi.reshape(ml * 4, 4 * mr)
+    col_lab = (lab_r[None, :, :] - SITE_Q[:, None, :]).reshape(-1, 2)
+    eig = _sector_eigs(X.T, col_lab)
+    kept = _select([e[2] for e in eig], M, cutoff)
+    rows_out, lab = [], []
+    for (q, cidx, w, u), kq in zip(eig, kept):
+        for t in range(kq):
+            r = np.zeros(4 * mr)
+            r[cidx] = u[:, t]
+            rows_out.append(r)
+            lab.append(q)
+    B = np.array(rows_out).reshape(len(rows_out), 4, mr)
+    C = (X @ B.reshape(len(rows_out), -1).T).reshape(ml, 4, -1)
+    total = sum(float(np.sum(e[2])) for e in eig)
+    keptw = sum(float(np.sum(e[2][:kq])) for e, kq in zip(eig, kept))
+    return B, C, np.array(lab, dtype=np.int64).reshape(-1, 2), total - keptw
+
+
+# --------------------------------------------------------------------------------- sweep
+class DMRG:
+    """Two-site DMRG driver.  Sweep = forward half over windows 0..n-2 followed by a
+    backward half over windows n-2..0.  After optimising window i the forward half splits
+    psi into A_i (left-canonical) and moves right (unless i = n-2); the backward half
+    splits into B_{i+1} (right-canonical) and moves left (unless i = 0).  The guess for the
+    next window is the split remainder contracted with the next site tensor."""
+
+    def __init__(self, mpo, bonds, sites):
+        self.mpo = mpo
+        self.n = mpo.n
+        self.lab, self.A = blocks_to_dense(bonds, sites)
+        n = self.n
+        self.L = [None] * (n + 1)
+        self.R = [None] * (n + 1)
+        self.L[0] = left_boundary()
+        self.R[n] = right_boundary()
+        for k in range(n - 1, 1, -1):
+            self.R[k] = right_env_update(self.R[k + 1], self.A[k], mpo.W[k],
+                                         mpo.parity[k + 1], len(mpo.chans[k]))
+        self.psi = np.einsum("asb,btc->astc", self.A[0], self.A[1])
+        self.stats = []
+
+    def heff(self, i):
+        return Heff(self.mpo, i, self.L[i], self.R[i + 2], self.lab[i])
+
+    def optimise(self, i, tol, max_iter, max_sub):
+        h = self.heff(i)
+        e, psi, nmv, rn2 = davidson(h.apply, h.diag(), self.psi, tol, max_iter, max_sub)
+        self.psi = psi
+        self.stats.append({"window": i, "energy": e, "n_matvec": nmv, "resid2": rn2})
+        return e
+
+    def move_right(self, i, M, cutoff):
+        A, C, lab, dw = left_split(self.psi, self.lab[i], M, cutoff)
+        self.A[i] = A
+        self.lab[i + 1] = lab
+        self.L[i + 1] = left_env_update(self.L[i], A, self.mpo.W[i], self.lab[i],
+                                        len(self.mpo.chans[i + 1]))
+        self.psi = np.einsum("asb,btc->astc", C, self.A[i + 2])
+        return dw
+
+    def move_left(self, i, M, cutoff):
+        B, C, lab, dw = right_split(self.psi, self.lab[i + 2], M, cutoff)
+        self.A[i + 1] = B
+        self.lab[i + 1] = lab
+        self.R[i + 1] = right_env_update(self.R[i + 2], B, self.mpo.W[i + 1],
+                                         self.mpo.parity[i + 2], len(self.mpo.chans[i + 1]))
+        self.psi = np.einsum("asb,btc->astc", self.A[i - 1], C)
+        return dw
+
+    def sweep(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+        n = self.n
+        dws = []
+        for i in range(0, n - 1):
+            self.optimise(i, tol, max_iter, max_sub)
+            if i < n - 2:
+                dws.append(self.move_right(i, M, cutoff))
+        for i in range(n - 2, -1, -1):
+            e = self.optimise(i, tol, max_iter, max_sub)
+            if i > 0:
+                dws.append(self.move_left(i, M, cutoff))
+        return e, max(dws) if dws else 0.0
+
+    def run(self, bond_dims, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+        energies = []
+        for M in bond_dims:
+            e, _ = self.sweep(M, tol, max_iter, max_sub, cutoff)
+            energies.append(e)
+        return energies
