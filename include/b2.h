@@ -1,0 +1,228 @@
+/*
+ * libb2 -- two-site DMRG hot path on one GB300 GPU (sm_103a).
+ *
+ * The method is ab initio two-site DMRG as described in the block2 paper (arXiv
+ * 2310.03920): an MPO for the Hamiltonian built from the integrals h_pq and (pq|rs)
+ * (Sec. 3.2), renormalized operators (environments) on both sides of a two-site window
+ * (Sec. 2.1.2 and Sec. 3.2, "renormalized operator view"), the effective Hamiltonian
+ * H_eff acting on the two-site wavefunction inside a Davidson eigensolver (Sec. 2.1.3
+ * (iv) "standard Davidson solver"; Listing 1: thrds, dav_max_iter), truncation of each
+ * bond to M states, and the sweep (Sec. 2.1.2).  Symmetry: particle number and projected
+ * spin, U(1) x U(1) ("SZ", Sec. 2.1.1).
+ *
+ * Conventions shared by every call
+ *   - Local site basis [|0>, |alpha>, |beta>, |alpha beta>] with (N, 2Sz) = (0,0), (1,1),
+ *     (1,-1), (2,0) and |alpha beta> = a+_alpha a+_beta |0> (Listing 1, Part A).
+ *   - Bond k lies between sites k-1 and k (k = 0..n).  Every bond sector is labelled by
+ *     the (N, 2Sz) of the LEFT block (sites 0..k-1).  Bond 0 has the one sector (0, 0);
+ *     bond n has the one sector (n_elec, two_sz); both of size 1.
+ *   - Site tensor k: blocks (jl, s, jr) with q[jl] + q(s) = q[jr], each a dense
+ *     row-major m_jl x m_jr FP64 array; blocks are stored in lexicographic (jl, s, jr)
+ *     order, concatenated.
+ *   - Two-site wavefunction of window (i, i+1) ("psi"): blocks (jl, s1, s2) with jl a
+ *     sector of bond i and jr (the sector of bond i+2 with q[jr] = q[jl] + q(s1) + q(s2))
+ *     existing; block (jl, s1, s2) is m_jl x m_jr row-major; blocks are ordered
+ *     lexicographically by (jl, s1, s2) and concatenated.  b2_psi_layout gives the size
+ *     and b2_psi_blocks the table.
+ *
+ * Memory and streams
+ *   - All handles are owned by the library and released with b2_free_* / b2_destroy.
+ *   - Host arrays passed in are copied during the call; the caller keeps ownership.
+ *   - Device pointers passed in (psi, out, diag) are owned by the caller, must be
+ *     8-byte aligned, live on the context's device, and are accessed on the context's
+ *     stream.  Calls are stream-ordered; results are ready when the stream is.
+ *   - Device memory the library needs is requested through the allocator callbacks given
+ *     to b2_create (PyTorch's caching allocator from the Python binding); when they are
+ *     NULL the library calls cudaMallocAsync / cudaFreeAsync on its stream.
+ *
+ * Errors: every int-returning call returns B2_OK or a negative code, checks its
+ * arguments before launching any kernel, never aborts the process, and leaves a message
+ * for b2_last_error.  Device-side waits are bounded; a wait that runs out reports
+ * B2_ETIMEOUT.
+ */
+#ifndef B2_H
+#define B2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  B2_OK = 0,
+  B2_EINVAL = -1,        /* invalid argument (shape, quantum numbers, aliasing, non-finite) */
+  B2_ENOMEM = -2,        /* an allocation failed */
+  B2_ECUDA = -3,         /* a CUDA runtime call failed */
+  B2_ENOCONV = -4,       /* an iterative solver did not converge where convergence is required */
+  B2_ETIMEOUT = -5,      /* a bounded device-side wait ran out */
+  B2_EUNSUPPORTED = -6   /* valid request this build does not implement */
+};
+
+/* Arithmetic of the H_eff contraction.  B2_FP64: FP64 throughout.  B2_BF16X3: each FP64
+ * operand split into bf16 hi + lo, products hi*hi + hi*lo + lo*hi on the tensor cores
+ * with FP32 accumulation, block results summed in FP64.  B2_BF16X6: three bf16 slices,
+ * the six products of order <= 2. */
+typedef enum { B2_FP64 = 0, B2_BF16X3 = 1, B2_BF16X6 = 2 } b2_prec;
+
+typedef struct b2_ctx_s* b2_ctx;
+typedef struct b2_mpo_s* b2_mpo;
+typedef struct b2_mps_s* b2_mps;
+typedef struct b2_env_s* b2_env;
+
+typedef void* (*b2_alloc_fn)(size_t bytes, void* user);
+typedef void (*b2_free_fn)(void* ptr, void* user);
+
+/* Context on CUDA device `device`, issuing all work on `stream` (a cudaStream_t owned by
+ * the caller; NULL = the legacy default stream).  alloc/free may be NULL (see above).
+ * *out is set only on success. */
+int b2_create(b2_ctx* out, int device, void* stream, b2_alloc_fn alloc, b2_free_fn free_fn,
+              void* user);
+void b2_destroy(b2_ctx ctx);
+/* Message of the last failed call on this context (owned by the library, valid until
+ * the next call); "" if none.  ctx may be NULL (message of the last b2_create). */
+const char* b2_last_error(b2_ctx ctx);
+
+/* ----------------------------------------------------------------------------- MPO
+ * Ab initio Hamiltonian (Sec. 2.1.1; formula H = E_core + sum_pq h_pq sum_s a+_ps a_qs
+ * + 1/2 sum_pqrs (pq|rs) sum_st a+_ps a+_rt a_st a_qs) as an exact MPO built from the
+ * operator strings (Sec. 3.2): operators with at most two elementary operators on the
+ * left of a bond are normal operators, the rest are carried as complementary operators,
+ * and the partition switches from normal/complementary to complementary/normal after
+ * the middle site (Sec. 3.2, "Symbolic MPO approach").
+ *   h1   host, n_orb x n_orb row-major, h1[p*n+q] = h_pq (symmetric)
+ *   eri  host, n_orb^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs)
+ *   integrals with |value| <= cutoff are dropped (0 keeps every nonzero)
+ * Errors: B2_EINVAL for n_orb < 2, n_orb > 64, non-finite integrals, or (n_elec, two_sz)
+ * impossible on n_orb orbitals. */
+int b2_build_mpo(b2_ctx ctx, int n_orb, const double* h1, const double* eri, double e_core,
+                 int n_elec, int two_sz, double cutoff, b2_mpo* out);
+/* Number of channels on every bond (bond_dims has n_orb + 1 entries). */
+int b2_mpo_info(b2_mpo mpo, int* n_orb, int* bond_dims);
+
+/* ----------------------------------------------------------------------------- MPS
+ * Import a block-sparse MPS (the layout above) from host arrays.
+ *   n_sectors   host, n+1 ints: sectors per bond
+ *   sectors     host, sum(n_sectors) x 3 ints (N, 2Sz, m), bond by bond, each bond's
+ *               sectors sorted by (N, 2Sz)
+ *   site_data   host, every site's blocks concatenated, site 0 first
+ *   center      canonical centre c: sites < c left-orthonormal, sites > c
+ *               right-orthonormal, site c carries the norm (not checked)
+ * Errors: B2_EINVAL for inconsistent sectors. */
+int b2_mps_import(b2_ctx ctx, int n, int n_elec, int two_sz, const int* n_sectors,
+                  const int* sectors, const double* site_data, int center, b2_mps* out);
+/* Sizes for b2_mps_export: total sectors (sum over bonds) and total FP64 elements. */
+int b2_mps_size(b2_mps mps, int64_t* n_sector_total, int64_t* n_elem_total, int* center);
+/* Copy the MPS back to host arrays sized by b2_mps_size (layout as for import). */
+int b2_mps_export(b2_ctx ctx, b2_mps mps, int* n_sectors, int* sectors, double* site_data);
+/* Random right-canonical MPS with sector sizes from per-spin occupation probabilities
+ * (Sec. 2.1.6 (ii): independent site occupancies give the initial quantum-number
+ * distribution; (i): random MPS).  occ: host, n_orb probabilities, or NULL for a Fermi
+ * function centred at N/2 of width 2.  The tensors are Gaussian (counter-based
+ * generator keyed by seed) made right-orthonormal on the GPU. */
+int b2_mps_random(b2_ctx ctx, b2_mpo mpo, int bond_dim, const double* occ, uint64_t seed,
+                  b2_mps* out);
+
+/* --------------------------------------------------------------------- environments
+ * Environments (renormalized operators, Sec. 3.2) of every MPO channel: all left
+ * environments L_0..L_center built from the left-orthonormal sites and all right
+ * environments R_{center+2}..R_n from the right-orthonormal sites.  The env keeps
+ * references to mpo and mps, which must outlive it. */
+int b2_env_init(b2_ctx ctx, b2_mpo mpo, b2_mps mps, int center, b2_env* out);
+/* One environment step with the MPS's current tensor at `site`:
+ *   dir = +1: L_{site+1} from L_site and site tensor `site` (left-orthonormal)
+ *   dir = -1: R_site from R_{site+1} and site tensor `site` (right-orthonormal) */
+int b2_env_update(b2_ctx ctx, b2_env env, int site, int dir);
+
+/* ------------------------------------------------------------ two-site effective H
+ * Layout of the two-site wavefunction of window (site, site+1): number of FP64 elements
+ * and of blocks.  The window's L_site and R_{site+2} must exist. */
+int b2_psi_layout(b2_ctx ctx, b2_env env, int site, int64_t* n_elem, int64_t* n_blocks);
+/* Block table of that layout: n_blocks x 6 int64 (jl, s1, s2, jr, offset, m_l*m_r). */
+int b2_psi_blocks(b2_ctx ctx, b2_env env, int site, int64_t* table);
+/* Two-site wavefunction of the MPS at window (site, site+1): the contraction of site
+ * tensors site and site+1, written to psi (device, n_elem FP64). */
+int b2_psi_from_mps(b2_ctx ctx, b2_env env, int site, double* psi);
+/* out = (H_eff - e_shift) psi for window (site, site+1) (Sec. 2.1.2; the operator is
+ * sum over MPO channel pairs of L_a (x) W_site W_{site+1} (x) R_b).  psi, out: device,
+ * n_elem FP64 each, must not overlap.  algo_flops (host, may be NULL) receives the
+ * algorithmic floating-point operations of the contraction (2 per multiply-add of the
+ * block GEMMs actually performed).  Errors: B2_EINVAL on overlap or bad site. */
+int b2_heff_apply(b2_ctx ctx, b2_env env, int site, const double* psi, double* out,
+                  b2_prec prec, double e_shift, double* algo_flops);
+/* Diagonal of H_eff for window (site, site+1) into diag (device, n_elem FP64): the
+ * Davidson preconditioner. */
+int b2_heff_diag(b2_ctx ctx, b2_env env, int site, double* diag);
+
+/* -------------------------------------------------------------------------- Davidson
+ * Lowest eigenpair of H_eff of window (site, site+1) by the Davidson method (Sec. 2.1.3
+ * (iv)): Rayleigh-Ritz in FP64 on the GPU, residual r = H v - theta v, converged when
+ * |r|^2 <= conv_tol; correction (D - theta)^-1 r with D the diagonal, orthogonalised
+ * twice; a full subspace restarts from the Ritz vector.  With prec != B2_FP64 the
+ * products use the split-precision contraction and the run is refined: the Ritz vector
+ * is re-checked with FP64 products until the FP64 residual meets conv_tol (or
+ * refine_max rounds), and the returned energy is the FP64 Rayleigh quotient.
+ *   psi   device, in: guess (need not be normalised), out: unit eigenvector
+ * Returns B2_OK also when max_iter is reached unconverged (check *resid2). */
+typedef struct {
+  int max_iter;       /* products with H_eff per solve (Listing 1: 30) */
+  int max_subspace;   /* subspace size before restart (30) */
+  double conv_tol;    /* |r|^2 threshold (Listing 1 thrds: 1e-10) */
+  b2_prec prec;
+  int refine_max;     /* FP64 refinement rounds for split precision (0 = default 4) */
+} b2_dav_opts;
+int b2_davidson(b2_ctx ctx, b2_env env, int site, double* psi, const b2_dav_opts* opts,
+                double* energy, int* n_matvec, double* resid2);
+
+/* ----------------------------------------------------------------------------- sweep
+ * Two-site DMRG sweeps (Sec. 2.1.2).  One sweep = a forward half over windows 0..n-2
+ * then a backward half over windows n-2..0.  After each window's Davidson the forward
+ * half splits psi into a left-orthonormal site tensor by the density matrix of the left
+ * part and moves right (except at window n-2); the backward half splits off a
+ * right-orthonormal tensor and moves left (except at window 0).  Each split keeps the M
+ * largest density-matrix eigenvalues over all sectors (eigenvalues <= trunc_cutoff *
+ * largest dropped; ties within 1e-14 * largest broken by sector order, then by order in
+ * the sector) using a batched FP64 Jacobi eigensolver on the GPU.  The next window's
+ * guess is the split remainder contracted with the next site tensor.  The env must have
+ * been made with center 0 for this mps, which must be in canonical form with centre 0;
+ * on return the MPS is again centred at site 0 and the env consistent with it. */
+typedef struct {
+  int n_sweeps;
+  const int* bond_dims;       /* host, n_sweeps entries: M of each sweep */
+  double conv_tol;            /* Davidson |r|^2 threshold */
+  int dav_max_iter;
+  int max_subspace;
+  b2_prec prec;
+  double trunc_cutoff;        /* relative eigenvalue cutoff, e.g. 1e-14 */
+} b2_sweep_opts;
+typedef struct {
+  double energy;              /* energy at the last window of the sweep */
+  double discarded_weight;    /* largest discarded weight of the sweep */
+  double seconds;             /* wall time of the sweep */
+  double matvec_flops;        /* algorithmic flops of all H_eff products of the sweep */
+  double other_flops;         /* algorithmic flops of environment updates and splits */
+  int n_matvec;
+  int max_bond;               /* largest bond dimension after the sweep */
+} b2_sweep_result;
+int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts* opts,
+             b2_sweep_result* per_sweep);
+
+/* ------------------------------------------------------------------ batched eigensolver
+ * Eigen-decomposition of n_mat real symmetric matrices by cyclic Jacobi rotations in
+ * FP64, one thread block per matrix: the density-matrix step of the truncation.
+ *   dims     host, n_mat ints (1..1024)
+ *   a        device, the matrices row-major and concatenated (sum dims^2 FP64); read only
+ *   evals    device, sum dims FP64: eigenvalues of each matrix in descending order
+ *   evecs    device, sum dims^2 FP64: row-major, column t is the eigenvector of evals[t] */
+int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, double* evals,
+                    double* evecs);
+
+void b2_free_mpo(b2_mpo mpo);
+void b2_free_mps(b2_mps mps);
+void b2_free_env(b2_env env);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* B2_H */

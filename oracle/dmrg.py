@@ -292,7 +292,7 @@ class DMRG:
     splits into B_{i+1} (right-canonical) and moves left (unless i = 0).  The guess for the
     next window is the split remainder contracted with the next site tensor."""
 
-    def __init__(self, mpo, bonds, sites):
+    def __init__(self, mpo, bonds, sites, center=0):
         self.mpo = mpo
         self.n = mpo.n
         self.lab, self.A = blocks_to_dense(bonds, sites)
@@ -301,10 +301,13 @@ class DMRG:
         self.R = [None] * (n + 1)
         self.L[0] = left_boundary()
         self.R[n] = right_boundary()
-        for k in range(n - 1, 1, -1):
+        for k in range(center):
+            self.L[k + 1] = left_env_update(self.L[k], self.A[k], mpo.W[k], self.lab[k],
+                                            len(mpo.chans[k + 1]))
+        for k in range(n - 1, center + 1, -1):
             self.R[k] = right_env_update(self.R[k + 1], self.A[k], mpo.W[k],
                                          mpo.parity[k + 1], len(mpo.chans[k]))
-        self.psi = np.einsum("asb,btc->astc", self.A[0], self.A[1])
+        self.psi = np.einsum("asb,btc->astc", self.A[center], self.A[center + 1])
         self.stats = []
 
     def heff(self, i):

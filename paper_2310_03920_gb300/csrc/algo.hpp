@@ -1,0 +1,23 @@
+// Davidson, truncation and sweep entry points (host orchestration).
+#pragma once
+
+#include "engine.hpp"
+
+namespace b2 {
+
+struct DavidsonResult {
+  double energy = 0, resid2 = 0, flops = 0;
+  int n_matvec = 0;
+};
+
+void contract_two_sites(Ctx* c, const Bond& ba, const Bond& bb, const SiteTensor& X,
+                        const double* xd, const SiteTensor& Y, const double* yd,
+                        const PsiLayout& lay, double* out, double* flops);
+DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o);
+void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
+                double* flops);
+void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
+                 double* flops, bool make_guess);
+void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res);
+
+}  // namespace b2

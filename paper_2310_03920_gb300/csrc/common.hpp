@@ -1,0 +1,163 @@
+// Internal declarations shared by the host-side translation units of libb2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/b2.h"
+
+namespace b2 {
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+#define B2_REQUIRE(cond, code, msg)                                   \
+  do {                                                                \
+    if (!(cond)) throw ::b2::Error((code), std::string(msg));         \
+  } while (0)
+#define B2_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw ::b2::Error(B2_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------- quantum numbers
+struct QN {
+  int n = 0, tsz = 0;
+  bool operator==(const QN& o) const { return n == o.n && tsz == o.tsz; }
+  bool operator<(const QN& o) const { return n < o.n || (n == o.n && tsz < o.tsz); }
+  QN operator+(const QN& o) const { return {n + o.n, tsz + o.tsz}; }
+  QN operator-(const QN& o) const { return {n - o.n, tsz - o.tsz}; }
+  int64_t key() const { return (int64_t(n) << 32) ^ int64_t(uint32_t(tsz)); }
+};
+extern const QN kSiteQ[4];    // |0>, |a>, |b>, |ab>
+extern const int kSiteN[4];
+
+// --------------------------------------------------------------------- context
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  b2_alloc_fn alloc = nullptr;
+  b2_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  std::string last_error;
+  int* d_status = nullptr;   // device status word for bounded waits (0 = ok)
+  void* raw_alloc(size_t bytes);
+  void raw_free(void* p);
+};
+
+// Device buffer owned by the library, allocated through the context.
+struct DevBuf {
+  Ctx* ctx = nullptr;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(Ctx* c, size_t b) { reset(c, b); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      ctx = o.ctx; ptr = o.ptr; bytes = o.bytes;
+      o.ptr = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void reset(Ctx* c, size_t b) {
+    release();
+    ctx = c;
+    bytes = b;
+    ptr = b ? c->raw_alloc(b) : nullptr;
+  }
+  void release() {
+    if (ptr && ctx) ctx->raw_free(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Upload a host vector into a (re)sized device buffer on the context stream.
+template <class T>
+void upload(Ctx* c, DevBuf& buf, const std::vector<T>& v) {
+  size_t b = v.size() * sizeof(T);
+  if (buf.bytes < b || buf.ptr == nullptr) buf.reset(c, b ? b : sizeof(T));
+  if (b) B2_CUDA(cudaMemcpyAsync(buf.ptr, v.data(), b, cudaMemcpyHostToDevice, c->stream));
+}
+
+// ---------------------------------------------------------------- bond table
+struct Bond {
+  std::vector<QN> q;
+  std::vector<int> m;
+  std::vector<int64_t> off;   // state offset of each sector (prefix sums of m)
+  std::unordered_map<int64_t, int> index;
+  int total = 0;
+  void finalize() {
+    off.assign(q.size() + 1, 0);
+    index.clear();
+    for (size_t j = 0; j < q.size(); ++j) {
+      off[j + 1] = off[j] + m[j];
+      index[q[j].key()] = int(j);
+    }
+    total = int(off.back());
+  }
+  int find(const QN& x) const {
+    auto it = index.find(x.key());
+    return it == index.end() ? -1 : it->second;
+  }
+  int size() const { return int(q.size()); }
+};
+
+// ---------------------------------------------------------- site tensor table
+struct SiteBlock {
+  int jl, s, jr;
+  int ml, mr;
+  int64_t off;   // element offset in the site buffer
+};
+struct SiteTensor {
+  std::vector<SiteBlock> blocks;
+  std::vector<int> lookup;   // lookup[jl * 4 + s] -> block index or -1
+  int64_t size = 0;
+  DevBuf data;
+  void build(const Bond& left, const Bond& right);   // all allowed blocks, sorted
+  int find(int jl, int s) const { return lookup[size_t(jl) * 4 + s]; }
+};
+
+}  // namespace b2
+
+// -------------------------------------------------------------- public handles
+struct b2_ctx_s {
+  b2::Ctx c;
+};
+
+struct b2_mpo_s {
+  int n = 0, n_elec = 0, two_sz = 0;
+  double e_core = 0.0;
+  std::vector<int> D;                                // channels per bond
+  std::vector<std::vector<int>> parity;              // per bond, per channel
+  std::vector<std::vector<b2::QN>> dq;               // per bond, per channel (left part)
+  struct Entry {
+    int w, w2;
+    double m[16];   // local operator, row = output state
+  };
+  std::vector<std::vector<Entry>> W;                 // per site
+};
+
+struct b2_mps_s {
+  b2::Ctx* ctx = nullptr;
+  int n = 0, n_elec = 0, two_sz = 0, center = 0;
+  std::vector<b2::Bond> bonds;          // n + 1
+  std::vector<b2::SiteTensor> sites;    // n
+};

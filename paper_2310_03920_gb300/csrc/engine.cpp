@@ -1,0 +1,570 @@
+// Environments (renormalized operators), the two-site effective Hamiltonian and its
+// diagonal, expressed as block-GEMM programs for the FP64 kernels (block2 paper: Sec.
+// 2.1.2 for the two-site wavefunction, Sec. 3.2 for the MPO / renormalized-operator
+// view).
+//
+// Fermion signs.  Every MPO channel w carries the parity p(w) of its left part.  On a ket
+// |l>|s> the product (left part)(site operator) costs (-1)^{p(op) N(l)}; on |s>|r> the
+// product (site operator)(right part w') costs (-1)^{p(w') n(s)}.  For the window (i, i+1)
+// the operator L_a (x) O1 (x) O2 (x) R_b on |l s1 s2 r> costs
+//   (-1)^{p(a) N(l)} * (-1)^{p(O2) n(s1)} * (-1)^{p(b) (n(s1) + n(s2))}
+// (the parities of the four factors add up to an even number).
+#include "engine.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+namespace b2 {
+
+using b2k::BufTable;
+using b2k::GemmTerm;
+using b2k::kTransP;
+using b2k::kTransQ;
+using b2k::kTwoOp;
+
+static inline int par_n(int n) { return n & 1; }
+
+// --------------------------------------------------------------- GemmProgram
+int GemmProgram::add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate) {
+  b2k::GemmOut o;
+  o.off = off;
+  o.M = M;
+  o.N = N;
+  o.ld = ld;
+  o.t0 = o.t1 = 0;
+  o.buf = buf;
+  o.accumulate = accumulate ? 1 : 0;
+  outs.push_back(o);
+  by_out.emplace_back();
+  return int(outs.size()) - 1;
+}
+
+void GemmProgram::add_term(int out, const GemmTerm& t) {
+  by_out[out].push_back(t);
+  const auto& o = outs[out];
+  if (t.flags & kTwoOp)
+    flops += 2.0 * o.M * t.K1 * o.N;
+  else
+    flops += 2.0 * o.M * t.K1 * t.K2 + 2.0 * o.M * double(t.K2) * o.N;
+}
+
+void GemmProgram::finalize(Ctx* c) {
+  terms.clear();
+  tiles.clear();
+  for (size_t i = 0; i < outs.size(); ++i) {
+    auto& o = outs[i];
+    o.t0 = int(terms.size());
+    terms.insert(terms.end(), by_out[i].begin(), by_out[i].end());
+    o.t1 = int(terms.size());
+    if (o.M == 0 || o.N == 0) continue;
+    if (o.accumulate && o.t0 == o.t1) continue;
+    for (int r = 0; r < o.M; r += b2k::kTile)
+      for (int cc = 0; cc < o.N; cc += b2k::kTile) tiles.push_back({int(i), r, cc});
+  }
+  B2_REQUIRE(terms.size() < (1u << 31), B2_EUNSUPPORTED, "too many contraction terms");
+  by_out.clear();
+  by_out.shrink_to_fit();
+  upload(c, d_terms, terms);
+  upload(c, d_outs, outs);
+  upload(c, d_tiles, tiles);
+}
+
+void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
+  b2k::launch_gemm(d_tiles.as<b2k::GemmTile>(), int(tiles.size()), d_outs.as<b2k::GemmOut>(),
+                   d_terms.as<GemmTerm>(), bt, c->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+void CombProgram::finalize(Ctx* c) {
+  tiles.clear();
+  for (size_t i = 0; i < outs.size(); ++i)
+    for (int64_t e = 0; e < outs[i].n; e += b2k::kCombChunk) tiles.push_back({int(i), e});
+  upload(c, d_terms, terms);
+  upload(c, d_outs, outs);
+  upload(c, d_tiles, tiles);
+}
+
+void CombProgram::launch(Ctx* c, const BufTable& bt) const {
+  b2k::launch_comb(d_tiles.as<b2k::CombTile>(), int(tiles.size()), d_outs.as<b2k::CombOut>(),
+                   d_terms.as<b2k::CombTerm>(), bt, c->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------- layouts
+void EnvBond::layout(const Bond& b, const std::vector<QN>& dq) {
+  blocks.clear();
+  blk.assign(dq.size(), std::vector<int>(b.size(), -1));
+  size = 0;
+  for (size_t w = 0; w < dq.size(); ++w)
+    for (int jk = 0; jk < b.size(); ++jk) {
+      int jb = b.find(b.q[jk] + dq[w]);
+      if (jb < 0) continue;
+      blk[w][jk] = int(blocks.size());
+      blocks.push_back({jb, jk, b.m[jb], b.m[jk], size});
+      size += int64_t(b.m[jb]) * b.m[jk];
+    }
+}
+
+void PsiLayout::build(const Bond& bl, const Bond& br) {
+  blocks.clear();
+  lookup.assign(size_t(bl.size()) * 16, -1);
+  size = 0;
+  for (int jl = 0; jl < bl.size(); ++jl)
+    for (int s1 = 0; s1 < 4; ++s1)
+      for (int s2 = 0; s2 < 4; ++s2) {
+        int jr = br.find(bl.q[jl] + kSiteQ[s1] + kSiteQ[s2]);
+        if (jr < 0) continue;
+        lookup[(size_t(jl) * 4 + s1) * 4 + s2] = int(blocks.size());
+        blocks.push_back({jl, s1, s2, jr, bl.m[jl], br.m[jr], size});
+        size += int64_t(bl.m[jl]) * br.m[jr];
+      }
+}
+
+static int op_parity(const double* m) {
+  for (int i = 0; i < 16; ++i)
+    if (m[i] != 0) return (kSiteN[i / 4] + kSiteN[i % 4]) & 1;
+  return 0;
+}
+
+// ----------------------------------------------------- operand precombination
+// An operand of a contraction: either one environment channel scaled by coef, or the
+// linear combination sum_c coef_c env[c] stored once in the combination buffer.  All
+// channels of one operand share their quantum-number shift, hence their block layout.
+struct Operand {
+  uint8_t buf;                   // 2/3: environment data, 4: combination buffer
+  std::vector<int64_t> off;      // per ket sector: block offset, -1 if absent
+  std::vector<int> bra;          // per ket sector: bra sector
+  double coef = 1.0;
+};
+
+struct Combiner {
+  CombProgram prog;
+  int64_t size = 0;
+  std::map<std::vector<std::pair<int, double>>, Operand> cache;
+
+  // env: the environment, buf its data id; list: (channel, coefficient)
+  Operand make(const EnvBond& env, uint8_t buf, const std::vector<std::pair<int, double>>& list) {
+    Operand op;
+    int ref = list[0].first;
+    const int nk = int(env.blk[ref].size());
+    op.off.assign(nk, -1);
+    op.bra.assign(nk, -1);
+    if (list.size() == 1) {
+      op.buf = buf;
+      op.coef = list[0].second;
+      for (int jk = 0; jk < nk; ++jk) {
+        int b = env.blk[ref][jk];
+        if (b < 0) continue;
+        op.off[jk] = env.blocks[b].off;
+        op.bra[jk] = env.blocks[b].jb;
+      }
+      return op;
+    }
+    auto key = list;
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    op.buf = 4;
+    for (int jk = 0; jk < nk; ++jk) {
+      int b = env.blk[ref][jk];
+      if (b < 0) continue;
+      const auto& blk = env.blocks[b];
+      op.off[jk] = size;
+      op.bra[jk] = blk.jb;
+      b2k::CombOut o;
+      o.off = size;
+      o.n = int64_t(blk.mb) * blk.mk;
+      o.buf = 4;
+      o.t0 = int(prog.terms.size());
+      for (auto& cw : list) {
+        int bb = env.blk[cw.first][jk];
+        B2_REQUIRE(bb >= 0 && env.blocks[bb].jb == blk.jb, B2_EINVAL,
+                   "internal: combined channels with different layouts");
+        prog.terms.push_back({env.blocks[bb].off, cw.second, buf});
+      }
+      o.t1 = int(prog.terms.size());
+      prog.outs.push_back(o);
+      size += o.n;
+    }
+    cache[key] = op;
+    return op;
+  }
+};
+
+// ------------------------------------------------------------ env updates
+static void check_env(const EnvBond& e, const char* what) {
+  B2_REQUIRE(e.valid, B2_EINVAL, std::string("environment not available: ") + what);
+}
+
+void env_update_left(b2_env_s* env, int k) {
+  b2_mpo_s* mpo = env->mpo;
+  b2_mps_s* mps = env->mps;
+  Ctx* c = env->ctx;
+  B2_REQUIRE(k >= 0 && k < mpo->n, B2_EINVAL, "site out of range");
+  EnvBond& Lk = env->L[k];
+  check_env(Lk, "L_site");
+  EnvBond& Lo = env->L[k + 1];
+  const Bond& bk = mps->bonds[k];
+  const Bond& bk1 = mps->bonds[k + 1];
+  const SiteTensor& A = mps->sites[k];
+  Lo.layout(bk1, mpo->dq[k + 1]);
+  Lo.data.reset(c, size_t(std::max<int64_t>(Lo.size, 1)) * sizeof(double));
+
+  std::map<std::tuple<int, int, int>, std::vector<std::pair<int, double>>> groups;
+  for (const auto& e : mpo->W[k])
+    for (int sp = 0; sp < 4; ++sp)
+      for (int s = 0; s < 4; ++s) {
+        double v = e.m[sp * 4 + s];
+        if (v != 0) groups[{e.w2, sp, s}].push_back({e.w, v});
+      }
+  GemmProgram prog;
+  std::vector<int> out_of(Lo.blocks.size());
+  for (size_t b = 0; b < Lo.blocks.size(); ++b) {
+    const auto& blk = Lo.blocks[b];
+    out_of[b] = prog.add_out(3, blk.off, blk.mb, blk.mk, blk.mk, false);
+  }
+  Combiner comb;
+  for (auto& g : groups) {
+    int w2 = std::get<0>(g.first), sp = std::get<1>(g.first), s = std::get<2>(g.first);
+    Operand op = comb.make(Lk, 2, g.second);
+    int odd = par_n(kSiteN[sp] + kSiteN[s]);
+    for (int jk = 0; jk < bk.size(); ++jk) {
+      if (op.off[jk] < 0) continue;
+      int jb = op.bra[jk];
+      int ab = A.find(jb, sp), ak = A.find(jk, s);
+      if (ab < 0 || ak < 0) continue;
+      const SiteBlock& Ab = A.blocks[ab];
+      const SiteBlock& Ak = A.blocks[ak];
+      int ob = Lo.find(w2, Ak.jr);
+      B2_REQUIRE(ob >= 0 && Lo.blocks[ob].jb == Ab.jr, B2_EINVAL, "internal: env layout");
+      double sign = (odd && par_n(bk.q[jk].n)) ? -1.0 : 1.0;
+      GemmTerm t{};
+      t.offP = Ab.off; t.bufP = 5; t.ldP = Ab.mr;        // op(P) = A^T  [m_jt' x m_jb]
+      t.offX = op.off[jk]; t.bufX = op.buf; t.ldX = bk.m[jk];   // X [m_jb x m_jk]
+      t.offQ = Ak.off; t.bufQ = 5; t.ldQ = Ak.mr;        // Q = A  [m_jk x m_jt]
+      t.K1 = bk.m[jb];
+      t.K2 = bk.m[jk];
+      t.flags = kTransP;
+      t.alpha = op.coef * sign;
+      prog.add_term(out_of[ob], t);
+    }
+  }
+  DevBuf cbuf;
+  BufTable bt{};
+  bt.p[2] = Lk.data.as<double>();
+  bt.p[3] = Lo.data.as<double>();
+  bt.p[5] = A.data.as<double>();
+  if (comb.size > 0) {
+    cbuf.reset(c, size_t(comb.size) * sizeof(double));
+    bt.p[4] = cbuf.as<double>();
+    comb.prog.finalize(c);
+    comb.prog.launch(c, bt);
+  }
+  prog.finalize(c);
+  prog.launch(c, bt);
+  Lo.valid = true;
+  Lo.version = ++env->version_counter;
+}
+
+void env_update_right(b2_env_s* env, int k) {
+  b2_mpo_s* mpo = env->mpo;
+  b2_mps_s* mps = env->mps;
+  Ctx* c = env->ctx;
+  B2_REQUIRE(k >= 0 && k < mpo->n, B2_EINVAL, "site out of range");
+  EnvBond& Rk1 = env->R[k + 1];
+  check_env(Rk1, "R_{site+1}");
+  EnvBond& Ro = env->R[k];
+  const Bond& bk = mps->bonds[k];
+  const Bond& bk1 = mps->bonds[k + 1];
+  const SiteTensor& B = mps->sites[k];
+  Ro.layout(bk, mpo->dq[k]);
+  Ro.data.reset(c, size_t(std::max<int64_t>(Ro.size, 1)) * sizeof(double));
+  // site blocks by (jr, s)
+  std::vector<int> rev(size_t(bk1.size()) * 4, -1);
+  for (size_t b = 0; b < B.blocks.size(); ++b) rev[size_t(B.blocks[b].jr) * 4 + B.blocks[b].s] = int(b);
+
+  std::map<std::tuple<int, int, int>, std::vector<std::pair<int, double>>> groups;
+  for (const auto& e : mpo->W[k])
+    for (int sp = 0; sp < 4; ++sp)
+      for (int s = 0; s < 4; ++s) {
+        double v = e.m[sp * 4 + s];
+        if (v != 0) groups[{e.w, sp, s}].push_back({e.w2, v});
+      }
+  GemmProgram prog;
+  std::vector<int> out_of(Ro.blocks.size());
+  for (size_t b = 0; b < Ro.blocks.size(); ++b) {
+    const auto& blk = Ro.blocks[b];
+    out_of[b] = prog.add_out(3, blk.off, blk.mb, blk.mk, blk.mk, false);
+  }
+  Combiner comb;
+  for (auto& g : groups) {
+    int w = std::get<0>(g.first), sp = std::get<1>(g.first), s = std::get<2>(g.first);
+    Operand op = comb.make(Rk1, 2, g.second);
+    int pw2 = mpo->parity[k + 1][g.second[0].first];
+    double sign = (pw2 && par_n(kSiteN[s])) ? -1.0 : 1.0;
+    for (int jrk = 0; jrk < bk1.size(); ++jrk) {
+      if (op.off[jrk] < 0) continue;
+      int jrb = op.bra[jrk];
+      int bb = rev[size_t(jrb) * 4 + sp], bkk = rev[size_t(jrk) * 4 + s];
+      if (bb < 0 || bkk < 0) continue;
+      const SiteBlock& Bb = B.blocks[bb];
+      const SiteBlock& Bk = B.blocks[bkk];
+      int ob = Ro.find(w, Bk.jl);
+      B2_REQUIRE(ob >= 0 && Ro.blocks[ob].jb == Bb.jl, B2_EINVAL, "internal: env layout");
+      GemmTerm t{};
+      t.offP = Bb.off; t.bufP = 5; t.ldP = Bb.mr;            // P = B [m_j' x m_jr']
+      t.offX = op.off[jrk]; t.bufX = op.buf; t.ldX = bk1.m[jrk];   // X [m_jr' x m_jr]
+      t.offQ = Bk.off; t.bufQ = 5; t.ldQ = Bk.mr;            // op(Q) = B^T [m_jr x m_j]
+      t.K1 = bk1.m[jrb];
+      t.K2 = bk1.m[jrk];
+      t.flags = kTransQ;
+      t.alpha = op.coef * sign;
+      prog.add_term(out_of[ob], t);
+    }
+  }
+  DevBuf cbuf;
+  BufTable bt{};
+  bt.p[2] = Rk1.data.as<double>();
+  bt.p[3] = Ro.data.as<double>();
+  bt.p[5] = B.data.as<double>();
+  if (comb.size > 0) {
+    cbuf.reset(c, size_t(comb.size) * sizeof(double));
+    bt.p[4] = cbuf.as<double>();
+    comb.prog.finalize(c);
+    comb.prog.launch(c, bt);
+  }
+  prog.finalize(c);
+  prog.launch(c, bt);
+  Ro.valid = true;
+  Ro.version = ++env->version_counter;
+}
+
+// ------------------------------------------------------------- window program
+namespace {
+struct Edge {
+  int a, b;
+  double v;
+};
+}  // namespace
+
+static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
+  b2_mpo_s* mpo = env->mpo;
+  b2_mps_s* mps = env->mps;
+  Ctx* c = env->ctx;
+  const EnvBond& L = env->L[i];
+  const EnvBond& R = env->R[i + 2];
+  const Bond& bl = mps->bonds[i];
+  const Bond& br = mps->bonds[i + 2];
+  wp = WindowProgram();
+  wp.site = i;
+  wp.ver_l = L.version;
+  wp.ver_r = R.version;
+  wp.psi.build(bl, br);
+
+  // two-site operators O_ab[u, v], u = 4 s1' + s2', v = 4 s1 + s2, with the sign of
+  // moving the site-(i+1) operator past s1 and the right part past s1 s2 folded in
+  std::vector<std::vector<int>> byw(mpo->D[i + 1]);
+  for (size_t e = 0; e < mpo->W[i + 1].size(); ++e) byw[mpo->W[i + 1][e].w].push_back(int(e));
+  std::map<std::pair<int, int>, std::map<int, double>> O;
+  for (const auto& e1 : mpo->W[i]) {
+    for (int e2i : byw[e1.w2]) {
+      const auto& e2 = mpo->W[i + 1][e2i];
+      int p2 = op_parity(e2.m);
+      int pb = mpo->parity[i + 2][e2.w2];
+      auto& dst = O[{e1.w, e2.w2}];
+      for (int a1 = 0; a1 < 16; ++a1) {
+        double x1 = e1.m[a1];
+        if (x1 == 0) continue;
+        int s1p = a1 / 4, s1 = a1 % 4;
+        for (int a2 = 0; a2 < 16; ++a2) {
+          double x2 = e2.m[a2];
+          if (x2 == 0) continue;
+          int s2p = a2 / 4, s2 = a2 % 4;
+          double sign = 1.0;
+          if (p2 && par_n(kSiteN[s1])) sign = -sign;
+          if (pb && par_n(kSiteN[s1] + kSiteN[s2])) sign = -sign;
+          dst[(s1p * 4 + s2p) * 16 + s1 * 4 + s2] += sign * x1 * x2;
+        }
+      }
+    }
+  }
+  // edges per local pattern (u, v)
+  std::map<int, std::vector<Edge>> pat;
+  for (auto& ab : O)
+    for (auto& uv : ab.second)
+      if (uv.second != 0) pat[uv.first].push_back({ab.first.first, ab.first.second, uv.second});
+
+  // outputs: every psi block, overwritten
+  GemmProgram& prog = wp.heff;
+  for (const auto& pb : wp.psi.blocks) prog.add_out(1, pb.off, pb.ml, pb.mr, pb.mr, false);
+  Combiner combL, combR;   // separate so the two combination regions can be concatenated
+  struct Pending {
+    Operand lop, rop;
+    int u, v;
+    int pL;
+    double coef;
+  };
+  std::vector<Pending> pending;
+  for (auto& pv : pat) {
+    int u = pv.first / 16, v = pv.first % 16;
+    auto& edges = pv.second;
+    // greedy vertex cover: highest degree first; each chosen vertex takes its remaining
+    // edges as one group (the other side is precombined)
+    std::map<int, int> dega, degb;
+    for (auto& e : edges) {
+      dega[e.a]++;
+      degb[e.b]++;
+    }
+    struct Vert {
+      int deg, side, id;
+    };
+    std::vector<Vert> verts;
+    for (auto& x : dega) verts.push_back({x.second, 0, x.first});
+    for (auto& x : degb) verts.push_back({x.second, 1, x.first});
+    std::stable_sort(verts.begin(), verts.end(), [](const Vert& x, const Vert& y) {
+      if (x.deg != y.deg) return x.deg > y.deg;
+      if (x.side != y.side) return x.side < y.side;
+      return x.id < y.id;
+    });
+    std::map<int, std::vector<int>> inc_a, inc_b;
+    for (size_t k = 0; k < edges.size(); ++k) {
+      inc_a[edges[k].a].push_back(int(k));
+      inc_b[edges[k].b].push_back(int(k));
+    }
+    std::vector<char> used(edges.size(), 0);
+    for (auto& vt : verts) {
+      auto& inc = vt.side == 0 ? inc_a[vt.id] : inc_b[vt.id];
+      std::vector<std::pair<int, double>> others;
+      for (int k : inc)
+        if (!used[k]) {
+          used[k] = 1;
+          others.push_back({vt.side == 0 ? edges[k].b : edges[k].a, edges[k].v});
+        }
+      if (others.empty()) continue;
+      Pending p;
+      p.u = u;
+      p.v = v;
+      if (vt.side == 0) {
+        p.lop = combL.make(L, 2, {{vt.id, 1.0}});
+        p.rop = combR.make(R, 3, others);
+        p.pL = mpo->parity[i][vt.id];
+      } else {
+        p.lop = combL.make(L, 2, others);
+        p.rop = combR.make(R, 3, {{vt.id, 1.0}});
+        p.pL = mpo->parity[i][others[0].first];
+      }
+      p.coef = p.lop.coef * p.rop.coef;
+      pending.push_back(std::move(p));
+    }
+  }
+  // the R combinations live after the L ones in the same buffer
+  int64_t shiftR = combL.size;
+  for (auto& o : combR.prog.outs) o.off += shiftR;
+  CombProgram& cp = wp.comb;
+  cp.outs = combL.prog.outs;
+  cp.terms = combL.prog.terms;
+  int tbase = int(cp.terms.size());
+  for (auto o : combR.prog.outs) {
+    o.t0 += tbase;
+    o.t1 += tbase;
+    cp.outs.push_back(o);
+  }
+  cp.terms.insert(cp.terms.end(), combR.prog.terms.begin(), combR.prog.terms.end());
+  for (auto& p : pending) {
+    if (p.rop.buf == 4)
+      for (auto& x : p.rop.off)
+        if (x >= 0) x += shiftR;
+    int s1p = p.u / 4, s2p = p.u % 4, s1 = p.v / 4, s2 = p.v % 4;
+    for (int jl = 0; jl < bl.size(); ++jl) {
+      int ib = wp.psi.find(jl, s1, s2);
+      if (ib < 0) continue;
+      const PsiBlock& in = wp.psi.blocks[ib];
+      if (p.lop.off[jl] < 0 || p.rop.off[in.jr] < 0) continue;
+      int jlp = p.lop.bra[jl], jrp = p.rop.bra[in.jr];
+      int ob = wp.psi.find(jlp, s1p, s2p);
+      if (ob < 0 || wp.psi.blocks[ob].jr != jrp) continue;
+      double sign = (p.pL && par_n(bl.q[jl].n)) ? -1.0 : 1.0;
+      GemmTerm t{};
+      t.offP = p.lop.off[jl]; t.bufP = p.lop.buf; t.ldP = in.ml;      // L [m_l' x m_l]
+      t.offX = in.off; t.bufX = 0; t.ldX = in.mr;                       // psi [m_l x m_r]
+      t.offQ = p.rop.off[in.jr]; t.bufQ = p.rop.buf; t.ldQ = in.mr;    // R [m_r' x m_r]
+      t.K1 = in.ml;
+      t.K2 = in.mr;
+      t.flags = kTransQ;
+      t.alpha = p.coef * sign;
+      prog.add_term(ob, t);
+    }
+  }
+  prog.finalize(c);
+  int64_t comb_size = combL.size + combR.size;
+  if (comb_size > 0) {
+    wp.comb_buf.reset(c, size_t(comb_size) * sizeof(double));
+    cp.finalize(c);
+  }
+
+  // diagonal: pairs whose channels keep the sector (diagonal blocks) and diagonal patterns
+  for (const auto& pb : wp.psi.blocks) {
+    b2k::DiagOut d;
+    d.off = pb.off;
+    d.ml = pb.ml;
+    d.mr = pb.mr;
+    d.t0 = int(wp.diag_terms.size());
+    int v = pb.s1 * 4 + pb.s2;
+    for (auto& ab : O) {
+      auto it = ab.second.find(v * 16 + v);
+      if (it == ab.second.end() || it->second == 0) continue;
+      int a = ab.first.first, b = ab.first.second;
+      int lb = L.blk[a][pb.jl], rb = R.blk[b][pb.jr];
+      if (lb < 0 || rb < 0) continue;
+      if (L.blocks[lb].jb != pb.jl || R.blocks[rb].jb != pb.jr) continue;
+      double sign = (mpo->parity[i][a] && par_n(bl.q[pb.jl].n)) ? -1.0 : 1.0;
+      wp.diag_terms.push_back({L.blocks[lb].off, R.blocks[rb].off, sign * it->second});
+    }
+    d.t1 = int(wp.diag_terms.size());
+    wp.diag_outs.push_back(d);
+  }
+  upload(c, wp.d_diag_outs, wp.diag_outs);
+  upload(c, wp.d_diag_terms, wp.diag_terms);
+  wp.comb_done = false;
+}
+
+WindowProgram& window_program(b2_env_s* env, int site) {
+  B2_REQUIRE(site >= 0 && site + 1 < env->mpo->n, B2_EINVAL, "window site out of range");
+  check_env(env->L[site], "L_site");
+  check_env(env->R[site + 2], "R_{site+2}");
+  auto& slot = env->windows[site];
+  if (!slot) slot.reset(new WindowProgram());
+  WindowProgram& wp = *slot;
+  if (wp.site != site || wp.ver_l != env->L[site].version || wp.ver_r != env->R[site + 2].version)
+    build_window(env, site, wp);
+  return wp;
+}
+
+void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
+                double* flops) {
+  WindowProgram& wp = window_program(env, site);
+  Ctx* c = env->ctx;
+  BufTable bt{};
+  bt.p[0] = const_cast<double*>(psi);
+  bt.p[1] = out;
+  bt.p[2] = env->L[site].data.as<double>();
+  bt.p[3] = env->R[site + 2].data.as<double>();
+  bt.p[4] = wp.comb_buf.as<double>();
+  if (!wp.comb_done) {
+    if (wp.comb_buf.ptr) wp.comb.launch(c, bt);
+    wp.comb_done = true;
+  }
+  wp.heff.launch(c, bt);
+  if (e_shift != 0.0) b2k::launch_axpby(out, psi, wp.psi.size, 1.0, -e_shift, c->stream);
+  if (flops) *flops = wp.heff.flops;
+}
+
+void heff_diag(b2_env_s* env, int site, double* diag) {
+  WindowProgram& wp = window_program(env, site);
+  b2k::launch_diag(int(wp.diag_outs.size()), wp.d_diag_outs.as<b2k::DiagOut>(),
+                   wp.d_diag_terms.as<b2k::DiagTerm>(), env->L[site].data.as<double>(),
+                   env->R[site + 2].data.as<double>(), diag, env->ctx->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+}  // namespace b2

@@ -1,0 +1,97 @@
+// Environments, contraction programs and the algorithms built on them.
+#pragma once
+
+#include <map>
+
+#include "common.hpp"
+#include "kernels.cuh"
+
+namespace b2 {
+
+// Block GEMM task list (see kernels.cuh) with its device copy.
+struct GemmProgram {
+  std::vector<std::vector<b2k::GemmTerm>> by_out;
+  std::vector<b2k::GemmOut> outs;
+  std::vector<b2k::GemmTerm> terms;
+  std::vector<b2k::GemmTile> tiles;
+  DevBuf d_terms, d_outs, d_tiles;
+  double flops = 0;
+  int add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate);
+  void add_term(int out, const b2k::GemmTerm& t);
+  void finalize(Ctx* c);
+  void launch(Ctx* c, const b2k::BufTable& bt) const;
+  bool empty() const { return tiles.empty(); }
+};
+
+struct CombProgram {
+  std::vector<b2k::CombOut> outs;
+  std::vector<b2k::CombTerm> terms;
+  std::vector<b2k::CombTile> tiles;
+  DevBuf d_terms, d_outs, d_tiles;
+  void finalize(Ctx* c);
+  void launch(Ctx* c, const b2k::BufTable& bt) const;
+};
+
+// Operator environment on one bond: every channel w has a block (j' <- j) for each ket
+// sector j whose bra sector j' (q[j'] = q[j] + dq(w)) exists; blocks are row-major.
+struct EnvBond {
+  bool valid = false;
+  int version = 0;
+  struct Blk {
+    int jb, jk, mb, mk;
+    int64_t off;
+  };
+  std::vector<Blk> blocks;
+  std::vector<std::vector<int>> blk;   // [w][jk] -> block index or -1
+  int64_t size = 0;
+  DevBuf data;
+  void layout(const Bond& b, const std::vector<QN>& dq);
+  int find(int w, int jk) const { return blk[w][jk]; }
+};
+
+struct PsiBlock {
+  int jl, s1, s2, jr, ml, mr;
+  int64_t off;
+};
+
+// Two-site wavefunction layout of window (i, i+1) on bonds i and i+2.
+struct PsiLayout {
+  std::vector<PsiBlock> blocks;
+  std::vector<int> lookup;   // [(jl * 4 + s1) * 4 + s2] -> block or -1
+  int64_t size = 0;
+  void build(const Bond& bl, const Bond& br);
+  int find(int jl, int s1, int s2) const { return lookup[(size_t(jl) * 4 + s1) * 4 + s2]; }
+};
+
+struct WindowProgram {
+  int site = -1;
+  int ver_l = -1, ver_r = -1;
+  PsiLayout psi;
+  GemmProgram heff;        // bufs: 0 psi, 1 out, 2 L env, 3 R env, 4 combination buffer
+  CombProgram comb;
+  DevBuf comb_buf;
+  std::vector<b2k::DiagOut> diag_outs;
+  std::vector<b2k::DiagTerm> diag_terms;
+  DevBuf d_diag_outs, d_diag_terms;
+  bool comb_done = false;
+};
+
+}  // namespace b2
+
+struct b2_env_s {
+  b2::Ctx* ctx = nullptr;
+  b2_mpo_s* mpo = nullptr;
+  b2_mps_s* mps = nullptr;
+  std::vector<b2::EnvBond> L, R;   // per bond
+  std::map<int, std::unique_ptr<b2::WindowProgram>> windows;
+  int version_counter = 0;
+};
+
+namespace b2 {
+WindowProgram& window_program(b2_env_s* env, int site);
+void env_update_left(b2_env_s* env, int site);
+void env_update_right(b2_env_s* env, int site);
+void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
+                double* flops);
+void heff_diag(b2_env_s* env, int site, double* diag);
+}  // namespace b2

@@ -1,0 +1,624 @@
+// FP64 kernels of libb2: block-sparse contractions, precombination of operators, the
+// H_eff diagonal, the batched Jacobi eigensolver, truncation selection, block copies and
+// the Davidson vector operations.  All loops over data are bounded by sizes passed in;
+// there are no device-side waits.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace b2k {
+
+// ============================================================ block GEMM (FP64)
+// One CTA of 128 threads owns a 32 x 32 tile of one output block and adds every term of
+// that block in order (no atomics, deterministic).  A 3-operand term is evaluated as
+// sum over 32-wide chunks c of K2 of (op(P) X[:, c]) op(Q)[c, :], keeping the
+// intermediate chunk in shared memory.
+__device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* M, int ld,
+                                          int rows, int cols, int r0, int c0, bool trans,
+                                          int tid) {
+  // S[i][j] = op(M)[r0 + i][c0 + j] (0 outside rows x cols); op(M) = M^T when trans
+  if (!trans) {
+    for (int e = tid; e < kTile * kTile; e += 128) {
+      int i = e >> 5, j = e & 31;
+      int r = r0 + i, c = c0 + j;
+      S[i][j] = (r < rows && c < cols) ? M[int64_t(r) * ld + c] : 0.0;
+    }
+  } else {
+    for (int e = tid; e < kTile * kTile; e += 128) {
+      int j = e >> 5, i = e & 31;
+      int r = r0 + i, c = c0 + j;
+      S[i][j] = (r < rows && c < cols) ? M[int64_t(c) * ld + r] : 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_gemm(const GemmTile* __restrict__ tiles,
+                                              const GemmOut* __restrict__ outs,
+                                              const GemmTerm* __restrict__ terms, BufTable bt) {
+  __shared__ double Ps[kTile][kTile + 1], Xs[kTile][kTile + 1];
+  __shared__ double Ts[kTile][kTile + 1], Qs[kTile][kTile + 1];
+  const GemmTile tile = tiles[blockIdx.x];
+  const GemmOut o = outs[tile.out];
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int r0 = tile.r0, c0 = tile.c0;
+  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int t = o.t0; t < o.t1; ++t) {
+    const GemmTerm g = terms[t];
+    const double* P = bt.p[g.bufP] + g.offP;
+    const double* X = bt.p[g.bufX] + g.offX;
+    const bool tP = g.flags & kTransP, tQ = g.flags & kTransQ;
+    double tacc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    if (g.flags & kTwoOp) {
+      for (int k0 = 0; k0 < g.K1; k0 += kTile) {
+        load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k0, tP, tid);
+        load_tile(Xs, X, g.ldX, g.K1, o.N, k0, c0, tQ, tid);
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kTile; ++kk) {
+          double a0 = Ps[2 * ty][kk], a1 = Ps[2 * ty + 1][kk];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            double x = Xs[kk][4 * tx + b];
+            tacc[0][b] = fma(a0, x, tacc[0][b]);
+            tacc[1][b] = fma(a1, x, tacc[1][b]);
+          }
+        }
+        __syncthreads();
+      }
+    } else {
+      const double* Q = bt.p[g.bufQ] + g.offQ;
+      for (int k2 = 0; k2 < g.K2; k2 += kTile) {
+        double tt[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        for (int k1 = 0; k1 < g.K1; k1 += kTile) {
+          load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k1, tP, tid);
+          load_tile(Xs, X, g.ldX, g.K1, g.K2, k1, k2, false, tid);
+          __syncthreads();
+#pragma unroll 8
+          for (int kk = 0; kk < kTile; ++kk) {
+            double a0 = Ps[2 * ty][kk], a1 = Ps[2 * ty + 1][kk];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              double x = Xs[kk][4 * tx + b];
+              tt[0][b] = fma(a0, x, tt[0][b]);
+              tt[1][b] = fma(a1, x, tt[1][b]);
+            }
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          Ts[2 * ty][4 * tx + b] = tt[0][b];
+          Ts[2 * ty + 1][4 * tx + b] = tt[1][b];
+        }
+        load_tile(Qs, Q, g.ldQ, g.K2, o.N, k2, c0, tQ, tid);
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kTile; ++kk) {
+          double a0 = Ts[2 * ty][kk], a1 = Ts[2 * ty + 1][kk];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            double x = Qs[kk][4 * tx + b];
+            tacc[0][b] = fma(a0, x, tacc[0][b]);
+            tacc[1][b] = fma(a1, x, tacc[1][b]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(g.alpha, tacc[a][b], acc[a][b]);
+  }
+  double* out = bt.p[o.buf] + o.off;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    int r = r0 + 2 * ty + a;
+    if (r >= o.M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int c = c0 + 4 * tx + b;
+      if (c >= o.N) continue;
+      double* p = out + int64_t(r) * o.ld + c;
+      *p = o.accumulate ? *p + acc[a][b] : acc[a][b];
+    }
+  }
+}
+
+void launch_gemm(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
+                 const BufTable& bt, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  k_gemm<<<n_tiles, 128, 0, s>>>(tiles, outs, terms, bt);
+}
+
+// =============================================================== precombination
+__global__ void __launch_bounds__(256) k_comb(const CombTile* __restrict__ tiles,
+                                              const CombOut* __restrict__ outs,
+                                              const CombTerm* __restrict__ terms, BufTable bt) {
+  const CombTile tile = tiles[blockIdx.x];
+  const CombOut o = outs[tile.out];
+  int64_t end = tile.e0 + kCombChunk;
+  if (end > o.n) end = o.n;
+  for (int64_t e = tile.e0 + threadIdx.x; e < end; e += 256) {
+    double acc = 0.0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const CombTerm c = terms[t];
+      acc = fma(c.c, bt.p[c.buf][c.off + e], acc);
+    }
+    bt.p[o.buf][o.off + e] = acc;
+  }
+}
+
+void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
+                 const BufTable& bt, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  k_comb<<<n_tiles, 256, 0, s>>>(tiles, outs, terms, bt);
+}
+
+// ======================================================================== diagonal
+__global__ void __launch_bounds__(128) k_diag(const DiagOut* __restrict__ outs,
+                                              const DiagTerm* __restrict__ terms,
+                                              const double* __restrict__ L,
+                                              const double* __restrict__ R, double* diag) {
+  const DiagOut o = outs[blockIdx.x];
+  const int n = o.ml * o.mr;
+  for (int e = threadIdx.x; e < n; e += 128) {
+    int l = e / o.mr, r = e % o.mr;
+    double acc = 0.0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const DiagTerm d = terms[t];
+      acc = fma(d.c * L[d.offL + int64_t(l) * o.ml + l], R[d.offR + int64_t(r) * o.mr + r], acc);
+    }
+    diag[o.off + e] = acc;
+  }
+}
+
+void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
+                 const double* R, double* diag, cudaStream_t s) {
+  if (n_out <= 0) return;
+  k_diag<<<n_out, 128, 0, s>>>(outs, terms, L, R, diag);
+}
+
+// =========================================================================== copy
+__global__ void __launch_bounds__(128) k_copy(const CopyTask* __restrict__ tasks, BufTable bt) {
+  const CopyTask c = tasks[blockIdx.x];
+  const double* src = bt.p[c.bsrc] + c.src;
+  double* dst = bt.p[c.bdst] + c.dst;
+  const int n = c.rows * c.cols;
+  for (int e = threadIdx.x; e < n; e += 128) {
+    int r = e / c.cols, k = e % c.cols;
+    dst[int64_t(r) * c.ldd + k] = c.trans ? src[int64_t(k) * c.lds + r] : src[int64_t(r) * c.lds + k];
+  }
+}
+
+void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s) {
+  if (n_tasks <= 0) return;
+  k_copy<<<n_tasks, 128, 0, s>>>(tasks, bt);
+}
+
+// ================================================================ batched Jacobi
+// Cyclic Jacobi for a real symmetric matrix (Golub & Van Loan, Matrix Computations,
+// Alg. 8.5.2 / 8.5.3 "sym.schur2" rotation; parallel round-robin ordering of the pivot
+// pairs so that each round's m/2 rotations touch disjoint rows and columns).  A rotation
+// is skipped when the off-diagonal element is negligible next to both diagonal entries
+// (100|a_pq| adds nothing to |a_pp| nor |a_qq|); the iteration stops after a sweep
+// without rotations (at most kMaxSweeps sweeps).
+constexpr int kJacobiSmemMax = 104;
+constexpr int kJacobiMaxDim = 1024;
+constexpr int kMaxSweeps = 60;
+
+__global__ void __launch_bounds__(256) k_jacobi(const int* __restrict__ dims,
+                                                const int64_t* __restrict__ offs,
+                                                const int64_t* __restrict__ eoffs,
+                                                const double* __restrict__ a, double* evals,
+                                                double* evecs, double* work,
+                                                const int64_t* __restrict__ woffs) {
+  extern __shared__ double smem[];
+  __shared__ int perm[kJacobiMaxDim], perm2[kJacobiMaxDim];
+  __shared__ double cs[kJacobiMaxDim / 2], sn[kJacobiMaxDim / 2];
+  __shared__ int pi_[kJacobiMaxDim / 2], qi_[kJacobiMaxDim / 2];
+  __shared__ int nrot;
+  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int m = dims[b];
+  double *A, *V;
+  if (m <= kJacobiSmemMax) {
+    A = smem;
+    V = smem + m * m;
+  } else {
+    A = work + woffs[b];
+    V = A + int64_t(m) * m;
+  }
+  const double* src = a + offs[b];
+  for (int e = tid; e < m * m; e += nt) {
+    A[e] = src[e];
+    V[e] = (e / m == e % m) ? 1.0 : 0.0;
+  }
+  const int mp = m + (m & 1), half = mp / 2;
+  for (int i = tid; i < mp; i += nt) perm[i] = i;
+  __syncthreads();
+  for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int i = tid; i < half; i += nt) {
+        int p = perm[i], q = perm[mp - 1 - i];
+        if (p > q) { int x = p; p = q; q = x; }
+        double c = 1.0, s = 0.0;
+        bool rot = false;
+        if (q < m) {
+          double apq = A[p * m + q];
+          if (apq != 0.0) {
+            double app = A[p * m + p], aqq = A[q * m + q];
+            double g = 100.0 * fabs(apq);
+            if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
+              double tau = (aqq - app) / (2.0 * apq);
+              double t = fabs(tau) > 1e150 ? 0.5 / tau
+                                           : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+              c = 1.0 / sqrt(1.0 + t * t);
+              s = t * c;
+              rot = true;
+            }
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+        pi_[i] = rot ? p : -1;
+        qi_[i] = q;
+        if (rot) atomicAdd(&nrot, 1);
+      }
+      __syncthreads();
+      for (int e = tid; e < half * m; e += nt) {   // rows: A <- J^T A
+        int i = e / m, k = e % m, p = pi_[i];
+        if (p < 0) continue;
+        int q = qi_[i];
+        double c = cs[i], s = sn[i];
+        double apk = A[p * m + k], aqk = A[q * m + k];
+        A[p * m + k] = c * apk - s * aqk;
+        A[q * m + k] = s * apk + c * aqk;
+      }
+      __syncthreads();
+      for (int e = tid; e < half * m; e += nt) {   // columns: A <- A J, V <- V J
+        int i = e / m, k = e % m, p = pi_[i];
+        if (p < 0) continue;
+        int q = qi_[i];
+        double c = cs[i], s = sn[i];
+        double akp = A[k * m + p], akq = A[k * m + q];
+        A[k * m + p] = c * akp - s * akq;
+        A[k * m + q] = s * akp + c * akq;
+        double vkp = V[k * m + p], vkq = V[k * m + q];
+        V[k * m + p] = c * vkp - s * vkq;
+        V[k * m + q] = s * vkp + c * vkq;
+      }
+      __syncthreads();
+      for (int i = tid; i < half; i += nt) {
+        int p = pi_[i];
+        if (p >= 0) {
+          int q = qi_[i];
+          A[p * m + q] = 0.0;
+          A[q * m + p] = 0.0;
+        }
+      }
+      for (int i = tid; i < mp; i += nt) {   // round-robin: keep perm[0], rotate the rest
+        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
+      }
+      __syncthreads();
+      for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
+      __syncthreads();
+    }
+    if (nrot == 0) break;
+    __syncthreads();
+  }
+  // descending order, ties by index
+  double* ev = evals + eoffs[b];
+  double* vec = evecs + offs[b];
+  for (int i = tid; i < m; i += nt) {
+    double di = A[i * m + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      double dj = A[j * m + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    ev[rank] = di;
+    for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = V[k * m + i];
+  }
+}
+
+void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
+                   const double* a, double* evals, double* evecs, double* work,
+                   const int64_t* woffs, int max_dim, cudaStream_t s) {
+  if (n_mat <= 0) return;
+  int sm_dim = max_dim <= kJacobiSmemMax ? max_dim : 0;
+  size_t smem = size_t(2) * sm_dim * sm_dim * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * kJacobiSmemMax * kJacobiSmemMax * int(sizeof(double)));
+    attr = true;
+  }
+  // matrices larger than the shared-memory limit work in global scratch (woffs)
+  if (max_dim > kJacobiSmemMax) smem = size_t(2) * kJacobiSmemMax * kJacobiSmemMax * sizeof(double);
+  k_jacobi<<<n_mat, 256, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs);
+}
+
+// ======================================================================= selection
+// Single CTA: bitonic sort of (value desc, id asc); chain neighbours closer than
+// 1e-14 * max into groups; re-sort by (group, id); keep the first M above cutoff * max.
+__device__ void bitonic_desc_val(double* key, int* id, int n2, int tid, int nt) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < n2; i += nt) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;   // "up" segment sorted descending by value
+          // a comes before b when (value larger) or (equal value and smaller id)
+          bool i_first = (key[i] > key[l]) || (key[i] == key[l] && id[i] < id[l]);
+          if (up != i_first) {
+            double tk = key[i]; key[i] = key[l]; key[l] = tk;
+            int ti = id[i]; id[i] = id[l]; id[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ void bitonic_asc_int(long long* key, int n2, int tid, int nt) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < n2; i += nt) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          if (up == (key[i] > key[l])) {
+            long long t = key[i]; key[i] = key[l]; key[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_select(int n, const double* __restrict__ vals,
+                                                 const int* __restrict__ sector, int n_sec,
+                                                 int M, double cutoff, int* kept, double* out) {
+  extern __shared__ unsigned char sm_raw[];
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  double* key = reinterpret_cast<double*>(sm_raw);
+  int* id = reinterpret_cast<int*>(key + n2);
+  long long* key2 = reinterpret_cast<long long*>(key);   // reused after the first sort
+  __shared__ double red[1024];
+  __shared__ double vmax_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n_sec; i += nt) kept[i] = 0;
+  double vmax = -DBL_MAX, tot = 0.0;
+  for (int i = tid; i < n2; i += nt) {
+    key[i] = i < n ? vals[i] : -DBL_MAX;
+    id[i] = i;
+    if (i < n) {
+      vmax = fmax(vmax, vals[i]);
+      tot += vals[i];
+    }
+  }
+  red[tid] = vmax;
+  __syncthreads();
+  for (int st = nt / 2; st > 0; st >>= 1) {
+    if (tid < st) red[tid] = fmax(red[tid], red[tid + st]);
+    __syncthreads();
+  }
+  if (tid == 0) vmax_s = red[0];
+  __syncthreads();
+  vmax = vmax_s;
+  // total weight in a fixed order (thread 0 sums sequentially for reproducibility)
+  __syncthreads();
+  bitonic_desc_val(key, id, n2, tid, nt);
+  // group ids by chaining neighbours: flag[i] = 1 if a new group starts at i
+  // prefix sum of flags -> group; store composite (group << 20 | id) in key2 afterwards
+  __shared__ int chunk_sum[1025];
+  int per = (n + nt - 1) / nt;
+  int lo = tid * per, hi = min(n, lo + per);
+  const double tol = 1e-14 * vmax;
+  int cnt = 0;
+  for (int i = lo; i < hi; ++i) cnt += (i == 0) || (key[i - 1] - key[i] > tol);
+  chunk_sum[tid + 1] = cnt;
+  if (tid == 0) chunk_sum[0] = 0;
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 1; i <= nt; ++i) chunk_sum[i] += chunk_sum[i - 1];
+  __syncthreads();
+  // compute groups into registers first (key is overwritten by key2 afterwards)
+  long long comp[32];
+  int g = chunk_sum[tid];
+  int nloc = 0;
+  for (int i = lo; i < hi && nloc < 32; ++i) {
+    g += (i == 0) || (key[i - 1] - key[i] > tol);
+    comp[nloc++] = ((long long)(g - 1) << 20) | (long long)id[i];
+  }
+  __syncthreads();
+  for (int i = lo, c = 0; i < hi && c < 32; ++i, ++c) key2[i] = comp[c];
+  for (int i = n + tid; i < n2; i += nt) key2[i] = LLONG_MAX;
+  __syncthreads();
+  bitonic_asc_int(key2, n2, tid, nt);
+  if (tid == 0) {
+    double kw = 0.0, all = 0.0;
+    for (int i = 0; i < n; ++i) all += vals[i];
+    for (int r = 0; r < n && r < M; ++r) {
+      int j = int(key2[r] & ((1 << 20) - 1));
+      if (vals[j] > cutoff * vmax) {
+        kept[sector[j]] += 1;
+        kw += vals[j];
+      }
+    }
+    out[0] = all - kw;
+    out[1] = kw;
+  }
+  (void)tot;
+}
+
+void launch_select(int n, const double* vals, const int* sector, int n_sec, int M,
+                   double cutoff, int* kept, double* out, cudaStream_t s) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  size_t smem = size_t(n2) * (sizeof(double) + sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSelectMax * int(sizeof(double) + sizeof(int)));
+    attr = true;
+  }
+  k_select<<<1, 1024, smem, s>>>(n, vals, sector, n_sec, M, cutoff, kept, out);
+}
+
+// ================================================================ Davidson vectors
+constexpr int kDotBlocks = 256;
+constexpr int kDotChunk = 16;
+
+__global__ void __launch_bounds__(256) k_multidot(int k, const double* __restrict__ vs, int64_t ld,
+                                                  const double* __restrict__ x, int64_t n,
+                                                  double* partial) {
+  __shared__ double red[kDotChunk][256 / 32];
+  const int tid = threadIdx.x;
+  double acc[kDotChunk];
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) acc[j] = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * 256 + tid; i < n; i += int64_t(gridDim.x) * 256) {
+    double xi = x[i];
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < k) acc[j] = fma(vs[j * ld + i], xi, acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[j][tid >> 5] = v;
+  }
+  __syncthreads();
+  if (tid < kDotChunk && tid < k) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[tid][w];
+    partial[int64_t(tid) * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+__global__ void k_reduce_partials(int k, const double* __restrict__ partial, int nblk, double* out,
+                                  int stride) {
+  __shared__ double red[256];
+  int j = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 256) v += partial[int64_t(j) * nblk + b];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[int64_t(j) * stride] = red[0];
+}
+
+void launch_multidot(int k, const double* vs, int64_t ld, const double* x, int64_t n,
+                     double* partial, double* out, int out_stride, cudaStream_t s) {
+  for (int j0 = 0; j0 < k; j0 += kDotChunk) {
+    int kk = k - j0 < kDotChunk ? k - j0 : kDotChunk;
+    k_multidot<<<kDotBlocks, 256, 0, s>>>(kk, vs + j0 * ld, ld, x, n, partial);
+    k_reduce_partials<<<kk, 256, 0, s>>>(kk, partial, kDotBlocks, out + int64_t(j0) * out_stride,
+                                         out_stride);
+  }
+}
+
+__global__ void k_multiaxpy(int k, const double* __restrict__ vs, int64_t ld,
+                            const double* __restrict__ c, double* y, int64_t n, double sign) {
+  __shared__ double cc[64];
+  if (threadIdx.x < k) cc[threadIdx.x] = c[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(cc[j], vs[j * ld + i], acc);
+    y[i] = fma(sign, acc, y[i]);
+  }
+}
+
+void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, double* y,
+                      int64_t n, double sign, cudaStream_t s) {
+  k_multiaxpy<<<1024, 256, 0, s>>>(k, vs, ld, c, y, n, sign);
+}
+
+__global__ void __launch_bounds__(256) k_ritz(int k, const double* __restrict__ V,
+                                              const double* __restrict__ W, int64_t ld,
+                                              const double* __restrict__ sv, int sld,
+                                              const double* __restrict__ theta_p,
+                                              const double* __restrict__ diag, double* u,
+                                              double* hu, double* t, int64_t n, double* partial) {
+  __shared__ double cc[64];
+  __shared__ double red[8];
+  if (threadIdx.x < k) cc[threadIdx.x] = sv[threadIdx.x * sld];
+  __syncthreads();
+  const double theta = *theta_p;
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < k; ++j) {
+      a = fma(cc[j], V[j * ld + i], a);
+      b = fma(cc[j], W[j * ld + i], b);
+    }
+    u[i] = a;
+    hu[i] = b;
+    double r = b - theta * a;
+    acc = fma(r, r, acc);
+    double den = diag[i] - theta;
+    if (fabs(den) < 1e-8) den = 1e-8;
+    t[i] = r / den;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w];
+    partial[blockIdx.x] = v;
+  }
+}
+
+void launch_ritz(int k, const double* V, const double* W, int64_t ld, const double* small_evecs,
+                 int small_ld, const double* theta, const double* diag, double* u, double* hu,
+                 double* t, int64_t n, double* partial, double* out, cudaStream_t s) {
+  k_ritz<<<kDotBlocks, 256, 0, s>>>(k, V, W, ld, small_evecs, small_ld, theta, diag, u, hu, t, n,
+                                    partial);
+  k_reduce_partials<<<1, 256, 0, s>>>(1, partial, kDotBlocks, out, 1);
+}
+
+__global__ void k_scale_inv_sqrt(double* x, int64_t n, const double* norm2) {
+  double f = 1.0 / sqrt(*norm2);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[i] *= f;
+}
+
+void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s) {
+  k_scale_inv_sqrt<<<1024, 256, 0, s>>>(x, n, norm2);
+}
+
+__global__ void k_axpby(double* x, const double* y, int64_t n, double a, double b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = a * x[i] + b * y[i];
+}
+
+void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cudaStream_t s) {
+  k_axpby<<<1024, 256, 0, s>>>(x, y, n, a, b);
+}
+
+__global__ void k_symmetrize(int k, const double* vw, int kmax, double* g) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    g[e] = 0.5 * (vw[i * kmax + j] + vw[j * kmax + i]);
+  }
+}
+
+void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s) {
+  k_symmetrize<<<1, 256, 0, s>>>(k, vw, kmax, g);
+}
+
+}  // namespace b2k

@@ -1,0 +1,118 @@
+// Device-side task formats and launchers of libb2's FP64 kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace b2k {
+
+constexpr int kMaxBufs = 8;
+struct BufTable {
+  double* p[kMaxBufs];
+};
+
+// One contribution to an output block:
+//   3-operand: out += alpha * op(P) [M x K1] * X [K1 x K2] * op(Q) [K2 x N]
+//   2-operand (flags & kTwoOp): out += alpha * op(P) [M x K1] * op(X) [K1 x N]
+// op(P) = P^T when flags & kTransP, op(Q) = Q^T when flags & kTransQ (2-operand: op(X) =
+// X^T when flags & kTransQ).  Matrices are row-major with leading dimensions ld*.
+enum : uint8_t { kTransP = 1, kTransQ = 2, kTwoOp = 4 };
+struct GemmTerm {
+  int64_t offP, offX, offQ;
+  int ldP, ldX, ldQ;
+  int K1, K2;
+  double alpha;
+  uint8_t bufP, bufX, bufQ, flags;
+};
+// An output block [M x N] (row-major, leading dimension ld) and its terms [t0, t1).
+struct GemmOut {
+  int64_t off;
+  int M, N, ld;
+  int t0, t1;
+  uint8_t buf, accumulate;   // accumulate = 0: out is overwritten
+};
+struct GemmTile {
+  int out, r0, c0;
+};
+constexpr int kTile = 32;
+
+// out[i] (+)= sum_t c_t * in_t[i] for i < n: precombination of operator blocks.
+struct CombTerm {
+  int64_t off;
+  double c;
+  int buf;
+};
+struct CombOut {
+  int64_t off, n;
+  int t0, t1;
+  int buf;
+};
+constexpr int kCombChunk = 2048;
+struct CombTile {
+  int out;
+  int64_t e0;
+};
+
+// diag block [ml x mr] (+)= sum_t c_t dL_t (x) dR_t, dL_t the diagonal of an ml x ml block,
+// dR_t the diagonal of an mr x mr block.
+struct DiagTerm {
+  int64_t offL, offR;
+  double c;
+};
+struct DiagOut {
+  int64_t off;
+  int ml, mr;
+  int t0, t1;
+};
+
+// Strided block copy: dst[r*ldd + c] = src[r*lds + c] (or src[c*lds + r] when trans).
+struct CopyTask {
+  int64_t src, dst;
+  int rows, cols, lds, ldd;
+  int trans;
+  uint8_t bsrc, bdst;
+};
+
+void launch_gemm(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
+                 const BufTable& bt, cudaStream_t s);
+void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
+                 const BufTable& bt, cudaStream_t s);
+void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
+                 const double* R, double* diag, cudaStream_t s);
+void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s);
+// Batched symmetric eigensolver; offs/voffs: element offsets of each matrix (dims^2 each)
+// and of its eigenvalues; work: scratch (sum dims^2 * 2 doubles) used for dims > 112.
+void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
+                   const double* a, double* evals, double* evecs, double* work,
+                   const int64_t* woffs, int max_dim, cudaStream_t s);
+// Global top-M selection over n eigenvalues (sector-major, descending in each sector).
+// sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
+// (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.
+// n <= kSelectMax.
+constexpr int kSelectMax = 16384;
+void launch_select(int n, const double* vals, const int* sector, int n_sec, int M,
+                   double cutoff, int* kept, double* out, cudaStream_t s);
+
+// Davidson vector kernels (n-long FP64 vectors, k <= 64 of them).
+// partial[j * nblk + b] = block b's part of dot(vs[j], x); then reduce to out[j] (with
+// out_stride).
+void launch_multidot(int k, const double* vs, int64_t ld, const double* x, int64_t n,
+                     double* partial, double* out, int out_stride, cudaStream_t s);
+// y = y - sum_j c[j] vs[j]   (c on device)
+void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, double* y,
+                      int64_t n, double sign, cudaStream_t s);
+// u = V s, hu = W s, r = hu - theta u; t = r / (D - theta) (|den| < 1e-8 -> 1e-8);
+// partial sums of |r|^2 into partial, reduced into out[0].  theta = evals[0], s = evec col 0.
+void launch_ritz(int k, const double* V, const double* W, int64_t ld, const double* small_evecs,
+                 int small_ld, const double* theta, const double* diag, double* u, double* hu,
+                 double* t, int64_t n, double* partial, double* out, cudaStream_t s);
+// x *= 1 / sqrt(*norm2)
+void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s);
+// x = alpha * y
+void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cudaStream_t s);
+// Build the symmetric k x k Rayleigh matrix from the stored overlaps: g[i*k+j] =
+// 0.5 (VW[i][j] + VW[j][i]), VW row-major with stride kmax.
+void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s);
+
+}  // namespace b2k

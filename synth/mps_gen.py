@@ -103,13 +103,15 @@ def sector_sizes(n, n_elec, two_sz, M, f):
     return [sorted((q[0], q[1], m) for q, m in b.items()) for b in bonds]
 
 
-def random_mps(bonds, seed):
-    """Right-canonical random MPS on the given sectors.
+def random_mps(bonds, seed, center=0):
+    """Random MPS on the given sectors, in canonical form with centre ``center``.
 
     Blocks are drawn N(0, 1) from ``default_rng(seed)`` site by site, in (jl, s) order.
-    Sites n-1 .. 1 are then made right-orthonormal by an LQ decomposition of each left
-    sector's row block (the L factor is pushed into the site on the left) and site 0 is
-    scaled to unit norm.  Returns a list of dicts {(jl, s, jr): array}.
+    Sites n-1 .. center+1 are then made right-orthonormal by an LQ decomposition of each
+    left sector's row block (the L factor is pushed into the site on the left), sites
+    0 .. center-1 left-orthonormal by a QR decomposition of each right sector's column
+    block (R pushed into the site on the right), and site ``center`` is scaled to unit
+    norm.  Returns a list of dicts {(jl, s, jr): array}.
     """
     rng = np.random.default_rng(seed)
     n = len(bonds) - 1
@@ -124,7 +126,20 @@ def random_mps(bonds, seed):
                     continue
                 blocks[(jl, s, jr)] = rng.standard_normal((ml, bonds[k + 1][jr][2]))
         sites.append(blocks)
-    for k in range(n - 1, 0, -1):
+    for k in range(center):
+        for jr in range(len(bonds[k + 1])):
+            keys = sorted(key for key in sites[k] if key[2] == jr)
+            x = np.vstack([sites[k][key] for key in keys])
+            qmat, rmat = np.linalg.qr(x)
+            row = 0
+            for key in keys:
+                h = sites[k][key].shape[0]
+                sites[k][key] = np.ascontiguousarray(qmat[row:row + h])
+                row += h
+            for key in sites[k + 1]:
+                if key[0] == jr:
+                    sites[k + 1][key] = rmat @ sites[k + 1][key]
+    for k in range(n - 1, center, -1):
         for jl in range(len(bonds[k])):
             keys = sorted(key for key in sites[k] if key[0] == jl)
             x = np.hstack([sites[k][key] for key in keys])
@@ -139,9 +154,9 @@ def random_mps(bonds, seed):
             for key in sites[k - 1]:
                 if key[2] == jl:
                     sites[k - 1][key] = sites[k - 1][key] @ lfac
-    norm = math.sqrt(sum(float(np.sum(b * b)) for b in sites[0].values()))
-    for key in sites[0]:
-        sites[0][key] = sites[0][key] / norm
+    norm = math.sqrt(sum(float(np.sum(b * b)) for b in sites[center].values()))
+    for key in sites[center]:
+        sites[center][key] = sites[center][key] / norm
     return sites
 
 
