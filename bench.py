@@ -1,0 +1,350 @@
+"""Benchmark of the two-site DMRG hot path on GB300.
+
+Workload (default): 1D Hubbard chain, L = 32 sites, t = 1, U = 4, open ends, half filling,
+Sz = 0, bond dimension M = 500, FP64 wavefunction.  One step = one full two-site sweep
+(forward and backward half) through the C-ABI (``b2_sweep``): every H_eff . psi product,
+H_eff diagonal, Davidson, density-matrix eigensolve, truncation and environment update.
+Inputs are synthetic (seeded integrals and random initial MPS); W warm-up sweeps bring the
+bonds to M before timing.
+
+metric/value: algorithmic H_eff . psi FLOP/s over the whole sweep (flops of the block
+GEMMs the contraction performs, summed over every product in the sweep, divided by the
+sweep's device time).  e2e: the same metric when each step also imports the MPS from host
+memory, builds the environments and exports the MPS back (host copies inside the timed
+region).  roofline: the H_eff contraction kernel, timed by CUDA events inside the library
+during the timed sweeps, against the FP64 peak measured on this GPU with cuBLAS DGEMM.
+
+``--impl reference`` times the CPU oracle (``oracle/``) on a bounded sample of the same
+workload (H_eff . psi products at the middle window) on the host cores.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torchrun with one
+process per GPU (independent replicas: the sweep does not shard).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff·ψ TFLOP/s & sweep time, mixed-prec vs FP64 on GB300 at |ΔE|≤1e-6 Eh"
+WORKLOAD = dict(name="hubbard_L32_U4_halffilling_M500_sweep", L=32, t=1.0, U=4.0, M=500,
+                mps_seed=1132)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload_inputs():
+    from synth import hubbard_integrals, occupancies, random_mps, sector_sizes
+    w = WORKLOAD
+    h, eri = hubbard_integrals(w["L"], w["t"], w["U"])
+    bonds = sector_sizes(w["L"], w["L"], 0, w["M"], occupancies(w["L"], w["L"], "hubbard"))
+    sites = random_mps(bonds, seed=w["mps_seed"])
+    return h, eri, bonds, sites
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks(torch):
+    """FP64 peak of this GPU (cuBLAS DGEMM through torch.matmul, 8192^3, best of 5) and the
+    measured HBM / bf16 figures."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks.update(json.load(f))
+    except OSError:
+        pass
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    peaks["fp64_tflops_measured"] = best
+    del a, b
+    torch.cuda.empty_cache()
+    return peaks
+
+
+def oracle_sample(budget_s, n_threads=None):
+    """The CPU oracle on a bounded sample of the workload: H_eff . psi products at the
+    middle window (sites 15, 16) of the same random MPS.  Returns (seconds per product,
+    number of products, setup seconds)."""
+    import numpy as np
+    from oracle import dmrg, mpo
+    h, eri, bonds, sites = workload_inputs()
+    from synth import random_mps
+    c = WORKLOAD["L"] // 2 - 1
+    sites_c = random_mps(bonds, seed=WORKLOAD["mps_seed"], center=c)
+    t0 = time.perf_counter()
+    d = dmrg.DMRG(mpo.MPO(h, eri), bonds, sites_c, center=c)
+    H = d.heff(c)
+    setup = time.perf_counter() - t0
+    x = d.psi
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t1 = time.perf_counter()
+        x = H.apply(x)
+        x /= np.linalg.norm(x)
+        times.append(time.perf_counter() - t1)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 50:
+            break
+    return statistics.median(times), len(times), setup, bonds, sites_c, c, h, eri
+
+
+def middle_window_flops(b2, ctx, h, eri, bonds, sites_c, c):
+    """Algorithmic flops of one H_eff . psi at the oracle sample's window (library count)."""
+    import torch
+    m = b2.b2_build_mpo(ctx, h, eri, 0.0, WORKLOAD["L"], 0)
+    s = b2.b2_mps_import(ctx, bonds, sites_c, WORKLOAD["L"], 0, center=c)
+    env = b2.b2_env_init(ctx, m, s, center=c)
+    n_elem, _ = b2.b2_psi_layout(ctx, env, c)
+    x = torch.ones(n_elem, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    fl = b2.b2_heff_apply(ctx, env, c, x, y)
+    b2.b2_free_env(env)
+    b2.b2_free_mps(s)
+    b2.b2_free_mpo(m)
+    return fl
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        blas = [i.get("num_threads") for i in info if i.get("user_api") == "blas"]
+        if blas:
+            return int(blas[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of the workload
+    (H_eff . psi products at the middle window, timed on the host cores).  The flop count
+    of one product is the library's count for the same window, the unit of the main arm."""
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    budget = max(2.0, args.cpu_budget)
+    sec, nprod, setup, bonds, sites_c, c, h, eri = oracle_sample(budget)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2310_03920_gb300 import b2
+    ctx = b2.Context(local)
+    fl = middle_window_flops(b2, ctx, h, eri, bonds, sites_c, c)
+    ctx.close()
+    value = fl / sec / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "L": WORKLOAD["L"], "U": WORKLOAD["U"],
+                       "M": WORKLOAD["M"], "sample": "H_eff.psi at the middle window"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
+                             "kind": "oracle",
+                             "sample": "%d oracle H_eff.psi products at window %d (setup %.1f s)"
+                                       % (nprod, c, setup)},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2310_03920_gb300 import b2
+
+    prec = b2.PRECISIONS[args.prec]
+    h, eri, bonds, sites = workload_inputs()
+    L, M = WORKLOAD["L"], WORKLOAD["M"]
+    ctx = b2.Context(local)
+    mpo_h = b2.b2_build_mpo(ctx, h, eri, 0.0, L, 0)
+    mps_h = b2.b2_mps_import(ctx, bonds, sites, L, 0, center=0)
+    env_h = b2.b2_env_init(ctx, mpo_h, mps_h, center=0)
+    # warm-up sweeps (bonds grow to M)
+    for _ in range(args.warmup):
+        b2.b2_sweep(ctx, mpo_h, mps_h, env_h, [M], prec=prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    energies, flops, step_ms = [], 0.0, []
+    b2.b2_profile(ctx, True)
+    barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # L2 flushed between steps (256 MB write)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = b2.b2_sweep(ctx, mpo_h, mps_h, env_h, [M], prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            energies.append(res[0]["energy"])
+            flops += res[0]["matvec_flops"]
+    barrier()
+    prof = b2.b2_profile_read(ctx)
+    b2.b2_profile(ctx, False)
+    t_step = sum(step_ms) / len(step_ms)
+    t_tot = sum(step_ms) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_tot, flops], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_tot, flops_all = float(mx[0]), float(tt[1])
+    else:
+        flops_all = flops
+    value = flops_all / t_tot / 1e12
+
+    # e2e through the public API from host buffers: import, env, one sweep, export
+    bonds_now, sites_now, _ = b2.b2_mps_export(ctx, mps_h)
+    h2d = sum(b.nbytes for blocks in sites_now for b in blocks.values())
+    e2e_ms, e2e_flops = [], 0.0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = b2.b2_mps_import(ctx, bonds_now, sites_now, L, 0, center=0)
+        en2 = b2.b2_env_init(ctx, mpo_h, s2, center=0)
+        r2 = b2.b2_sweep(ctx, mpo_h, s2, en2, [M], prec=prec)
+        out = b2.b2_mps_export(ctx, s2)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_flops += r2[0]["matvec_flops"]
+        d2h = sum(b.nbytes for blocks in out[1] for b in blocks.values())
+        b2.b2_free_env(en2)
+        b2.b2_free_mps(s2)
+    e2e_val = e2e_flops / (sum(e2e_ms) * 1e-3) / 1e12
+
+    if rank != 0:
+        return
+    peaks = measured_peaks(torch)
+    fp64_peak = peaks["fp64_tflops_measured"]
+    achieved = (prof["heff_flops"] / (prof["heff_ms"] * 1e-3) / 1e12) if prof["heff_ms"] > 0 else 0.0
+    roofline = {"kernel": "k_gemm (H_eff block contraction, FP64)", "bound": "alu",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if fp64_peak else None,
+                "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU",
+                "launches": prof["heff_launches"],
+                "avg_launch_us": prof["heff_ms"] * 1e3 / max(1, prof["heff_launches"]),
+                "traffic": None}
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "L": L, "t": WORKLOAD["t"], "U": WORKLOAD["U"],
+                       "n_elec": L, "two_sz": 0, "M": M, "prec": args.prec,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "sweep_energy": energies[-1], "sweep_ms": step_ms,
+            "roofline": roofline, "gpu_launches": int(prof["launches"]),
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": statistics.mean(e2e_ms),
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    if not args.no_cpu_baseline and world == 1:
+        budget = args.cpu_budget
+        sec, nprod, setup, bonds_c, sites_c, c, h_, eri_ = oracle_sample(budget)
+        fl = middle_window_flops(b2, ctx, h, eri, bonds_c, sites_c, c)
+        line["cpu_baseline"] = {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": "%d oracle H_eff.psi products at the middle window "
+                                          "(sites %d, %d) of the same workload; setup %.1f s"
+                                          % (nprod, c, c + 1, setup)}
+    print(json.dumps(line), flush=True)
+    b2.b2_free_env(env_h)
+    b2.b2_free_mps(mps_h)
+    b2.b2_free_mpo(mpo_h)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

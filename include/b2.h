@@ -218,6 +218,20 @@ int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts
 int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, double* evals,
                     double* evecs);
 
+/* ------------------------------------------------------------------------ profiling
+ * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every
+ * launch of the H_eff contraction kernel is bracketed by CUDA events on the context
+ * stream, and every kernel launch of the library is counted.  b2_profile(ctx, 1) also
+ * resets the counters. */
+typedef struct {
+  int64_t launches;        /* kernel launches of the library since the reset */
+  int64_t heff_launches;   /* H_eff contraction kernel launches timed */
+  double heff_ms;          /* their summed device time */
+  double heff_flops;       /* their summed algorithmic flops */
+} b2_profile_data;
+int b2_profile(b2_ctx ctx, int enable);
+int b2_profile_read(b2_ctx ctx, b2_profile_data* out);
+
 void b2_free_mpo(b2_mpo mpo);
 void b2_free_mps(b2_mps mps);
 void b2_free_env(b2_env env);

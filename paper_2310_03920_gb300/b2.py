@@ -43,6 +43,10 @@ class SweepResult(ctypes.Structure):
                 ("other_flops", _d), ("n_matvec", _i), ("max_bond", _i)]
 
 
+class ProfileData(ctypes.Structure):
+    _fields_ = [("launches", _i64), ("heff_launches", _i64), ("heff_ms", _d), ("heff_flops", _d)]
+
+
 _sig = {
     "b2_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _ALLOC, _FREE, _vp]),
     "b2_destroy": (None, [_vp]),
@@ -64,6 +68,8 @@ _sig = {
                          ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "b2_sweep": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepResult)]),
     "b2_eigh_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "b2_profile": (_i, [_vp, _i]),
+    "b2_profile_read": (_i, [_vp, ctypes.POINTER(ProfileData)]),
     "b2_free_mpo": (None, [_vp]),
     "b2_free_mps": (None, [_vp]),
     "b2_free_env": (None, [_vp]),
@@ -252,6 +258,16 @@ def b2_sweep(ctx, mpo, mps, env, bond_dims, conv_tol=1e-10, dav_max_iter=30, max
 def b2_eigh_batched(ctx, dims, a, evals, evecs):
     d = np.ascontiguousarray(dims, dtype=np.int32)
     _check(ctx.h, lib.b2_eigh_batched(ctx.h, len(d), d.ctypes.data, _ptr(a), _ptr(evals), _ptr(evecs)))
+
+
+def b2_profile(ctx, enable=True):
+    _check(ctx.h, lib.b2_profile(ctx.h, 1 if enable else 0))
+
+
+def b2_profile_read(ctx):
+    d = ProfileData()
+    _check(ctx.h, lib.b2_profile_read(ctx.h, ctypes.byref(d)))
+    return {f: getattr(d, f) for f, _ in ProfileData._fields_}
 
 
 def b2_free_mpo(mpo):

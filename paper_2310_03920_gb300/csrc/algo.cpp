@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "algo.hpp"
 
@@ -108,6 +110,9 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
                             c->stream));
     sync(c);
     res.resid2 = host_sc[0];
+    if (std::getenv("B2_TRACE_DAVIDSON"))
+      std::fprintf(stderr, "davidson site %d k %d nmv %d theta %.15f r2 %.3e\n", site, k, nmv,
+                   res.energy, res.resid2);
     B2_REQUIRE(std::isfinite(res.resid2) && std::isfinite(res.energy), B2_ENOCONV,
                "Davidson produced a non-finite value");
     if (res.resid2 <= o.conv_tol || nmv >= max_iter) break;

@@ -82,6 +82,7 @@ int b2_create(b2_ctx* out, int device, void* stream, b2_alloc_fn alloc, b2_free_
 void b2_destroy(b2_ctx ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->c.stream);
+  ctx->c.prof_clear();
   delete ctx;
 }
 
@@ -308,6 +309,33 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
                        work.as<double>(), dwoff.as<int64_t>(), max_dim, c->stream);
     B2_CUDA(cudaGetLastError());
     B2_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+int b2_profile(b2_ctx ctx, int enable) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(ctx, B2_EINVAL, "null context");
+    B2_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    ctx->c.prof_clear();
+    ctx->c.prof = enable != 0;
+    ctx->c.launch_base = b2k::launch_count();
+  });
+}
+
+int b2_profile_read(b2_ctx ctx, b2_profile_data* out) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(ctx && out, B2_EINVAL, "null argument");
+    B2_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    double ms = 0;
+    for (auto& e : ctx->c.prof_events) {
+      float t = 0;
+      B2_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+      ms += t;
+    }
+    out->launches = b2k::launch_count() - ctx->c.launch_base;
+    out->heff_launches = int64_t(ctx->c.prof_events.size());
+    out->heff_ms = ms;
+    out->heff_flops = ctx->c.prof_flops;
   });
 }
 

@@ -52,8 +52,21 @@ struct Ctx {
   void* user = nullptr;
   std::string last_error;
   int* d_status = nullptr;   // device status word for bounded waits (0 = ok)
+  // benchmark profiling (b2_profile): events around H_eff kernel launches
+  bool prof = false;
+  long long launch_base = 0;
+  double prof_flops = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   void* raw_alloc(size_t bytes);
   void raw_free(void* p);
+  void prof_clear() {
+    for (auto& e : prof_events) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    prof_events.clear();
+    prof_flops = 0;
+  }
 };
 
 // Device buffer owned by the library, allocated through the context.

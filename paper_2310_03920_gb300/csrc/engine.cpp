@@ -554,7 +554,18 @@ void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double 
     if (wp.comb_buf.ptr) wp.comb.launch(c, bt);
     wp.comb_done = true;
   }
-  wp.heff.launch(c, bt);
+  if (c->prof) {
+    cudaEvent_t e0, e1;
+    B2_CUDA(cudaEventCreate(&e0));
+    B2_CUDA(cudaEventCreate(&e1));
+    B2_CUDA(cudaEventRecord(e0, c->stream));
+    wp.heff.launch(c, bt);
+    B2_CUDA(cudaEventRecord(e1, c->stream));
+    c->prof_events.push_back({e0, e1});
+    c->prof_flops += wp.heff.flops;
+  } else {
+    wp.heff.launch(c, bt);
+  }
   if (e_shift != 0.0) b2k::launch_axpby(out, psi, wp.psi.size, 1.0, -e_shift, c->stream);
   if (flops) *flops = wp.heff.flops;
 }

@@ -2,12 +2,18 @@
 // H_eff diagonal, the batched Jacobi eigensolver, truncation selection, block copies and
 // the Davidson vector operations.  All loops over data are bounded by sizes passed in;
 // there are no device-side waits.
+#include <atomic>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "kernels.cuh"
 
 namespace b2k {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launches(int n) { g_launches += n; }
 
 // ============================================================ block GEMM (FP64)
 // One CTA of 128 threads owns a 32 x 32 tile of one output block and adds every term of
@@ -130,6 +136,7 @@ void launch_gemm(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const 
                  const BufTable& bt, cudaStream_t s) {
   if (n_tiles <= 0) return;
   k_gemm<<<n_tiles, 128, 0, s>>>(tiles, outs, terms, bt);
+  g_launches += 1;
 }
 
 // =============================================================== precombination
@@ -154,6 +161,7 @@ void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const 
                  const BufTable& bt, cudaStream_t s) {
   if (n_tiles <= 0) return;
   k_comb<<<n_tiles, 256, 0, s>>>(tiles, outs, terms, bt);
+  g_launches += 1;
 }
 
 // ======================================================================== diagonal
@@ -178,6 +186,7 @@ void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const do
                  const double* R, double* diag, cudaStream_t s) {
   if (n_out <= 0) return;
   k_diag<<<n_out, 128, 0, s>>>(outs, terms, L, R, diag);
+  g_launches += 1;
 }
 
 // =========================================================================== copy
@@ -195,6 +204,7 @@ __global__ void __launch_bounds__(128) k_copy(const CopyTask* __restrict__ tasks
 void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s) {
   if (n_tasks <= 0) return;
   k_copy<<<n_tasks, 128, 0, s>>>(tasks, bt);
+  g_launches += 1;
 }
 
 // ================================================================ batched Jacobi
@@ -339,6 +349,7 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
   // matrices larger than the shared-memory limit work in global scratch (woffs)
   if (max_dim > kJacobiSmemMax) smem = size_t(2) * kJacobiSmemMax * kJacobiSmemMax * sizeof(double);
   k_jacobi<<<n_mat, 256, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs);
+  g_launches += 1;
 }
 
 // ======================================================================= selection
@@ -468,6 +479,7 @@ void launch_select(int n, const double* vals, const int* sector, int n_sec, int 
     attr = true;
   }
   k_select<<<1, 1024, smem, s>>>(n, vals, sector, n_sec, M, cutoff, kept, out);
+  g_launches += 1;
 }
 
 // ================================================================ Davidson vectors
@@ -522,8 +534,10 @@ void launch_multidot(int k, const double* vs, int64_t ld, const double* x, int64
   for (int j0 = 0; j0 < k; j0 += kDotChunk) {
     int kk = k - j0 < kDotChunk ? k - j0 : kDotChunk;
     k_multidot<<<kDotBlocks, 256, 0, s>>>(kk, vs + j0 * ld, ld, x, n, partial);
+    g_launches += 1;
     k_reduce_partials<<<kk, 256, 0, s>>>(kk, partial, kDotBlocks, out + int64_t(j0) * out_stride,
                                          out_stride);
+    g_launches += 1;
   }
 }
 
@@ -543,6 +557,7 @@ __global__ void k_multiaxpy(int k, const double* __restrict__ vs, int64_t ld,
 void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, double* y,
                       int64_t n, double sign, cudaStream_t s) {
   k_multiaxpy<<<1024, 256, 0, s>>>(k, vs, ld, c, y, n, sign);
+  g_launches += 1;
 }
 
 __global__ void __launch_bounds__(256) k_ritz(int k, const double* __restrict__ V,
@@ -586,7 +601,9 @@ void launch_ritz(int k, const double* V, const double* W, int64_t ld, const doub
                  double* t, int64_t n, double* partial, double* out, cudaStream_t s) {
   k_ritz<<<kDotBlocks, 256, 0, s>>>(k, V, W, ld, small_evecs, small_ld, theta, diag, u, hu, t, n,
                                     partial);
+  g_launches += 1;
   k_reduce_partials<<<1, 256, 0, s>>>(1, partial, kDotBlocks, out, 1);
+  g_launches += 1;
 }
 
 __global__ void k_scale_inv_sqrt(double* x, int64_t n, const double* norm2) {
@@ -598,6 +615,7 @@ __global__ void k_scale_inv_sqrt(double* x, int64_t n, const double* norm2) {
 
 void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s) {
   k_scale_inv_sqrt<<<1024, 256, 0, s>>>(x, n, norm2);
+  g_launches += 1;
 }
 
 __global__ void k_axpby(double* x, const double* y, int64_t n, double a, double b) {
@@ -608,6 +626,7 @@ __global__ void k_axpby(double* x, const double* y, int64_t n, double a, double 
 
 void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cudaStream_t s) {
   k_axpby<<<1024, 256, 0, s>>>(x, y, n, a, b);
+  g_launches += 1;
 }
 
 __global__ void k_symmetrize(int k, const double* vw, int kmax, double* g) {
@@ -619,6 +638,7 @@ __global__ void k_symmetrize(int k, const double* vw, int kmax, double* g) {
 
 void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s) {
   k_symmetrize<<<1, 256, 0, s>>>(k, vw, kmax, g);
+  g_launches += 1;
 }
 
 }  // namespace b2k

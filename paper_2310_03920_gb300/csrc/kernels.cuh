@@ -7,6 +7,10 @@
 
 namespace b2k {
 
+// Number of kernels launched by this library in this process (all threads).
+long long launch_count();
+void count_launches(int n);
+
 constexpr int kMaxBufs = 8;
 struct BufTable {
   double* p[kMaxBufs];
