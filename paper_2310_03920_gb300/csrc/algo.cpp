@@ -54,14 +54,16 @@ void contract_two_sites(Ctx* c, const Bond& ba, const Bond& bb, const SiteTensor
 }
 
 // ------------------------------------------------------------------- Davidson
-DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o) {
+// Davidson with products in precision mv_prec.  When w0 is given it is H psi / |psi| (an
+// FP64 product of the normalised start vector, computed by the caller) and seeds W[0].
+static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const b2_dav_opts& o,
+                                    b2_prec mv_prec, const double* w0, double tol) {
   Ctx* c = env->ctx;
   WindowProgram& wp = window_program(env, site);
   const int64_t n = wp.psi.size;
   B2_REQUIRE(n > 0, B2_EINVAL, "empty two-site wavefunction");
   const int kmax = std::max(2, std::min(o.max_subspace > 0 ? o.max_subspace : 30, 64));
   const int max_iter = o.max_iter > 0 ? o.max_iter : 30;
-  B2_REQUIRE(o.prec == B2_FP64, B2_EUNSUPPORTED, "only FP64 Davidson in this build");
   DevBuf V(c, sizeof(double) * n * kmax), W(c, sizeof(double) * n * kmax);
   DevBuf diag(c, sizeof(double) * n), u(c, sizeof(double) * n), hu(c, sizeof(double) * n),
       t(c, sizeof(double) * n);
@@ -86,9 +88,14 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
   b2k::launch_multidot(1, psi, n, psi, n, part, scal + 2, 1, c->stream);
   B2_CUDA(cudaMemcpyAsync(Vp, psi, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   b2k::launch_scale_inv_sqrt(Vp, n, scal + 2, c->stream);
-  heff_apply(env, site, Vp, Wp, 0.0, &fl);
-  res.flops += fl;
-  int nmv = 1, k = 1;
+  int nmv = 0, k = 1;
+  if (w0) {
+    B2_CUDA(cudaMemcpyAsync(Wp, w0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    heff_apply(env, site, Vp, Wp, 0.0, &fl, mv_prec);
+    res.flops += fl;
+    nmv = 1;
+  }
   b2k::launch_multidot(1, Vp, n, Wp, n, part, VW, 1, c->stream);
   // small eigensolver metadata: dims / offsets for the single k x k problem
   int dims_h[1];
@@ -115,7 +122,9 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
                    res.energy, res.resid2);
     B2_REQUIRE(std::isfinite(res.resid2) && std::isfinite(res.energy), B2_ENOCONV,
                "Davidson produced a non-finite value");
-    if (res.resid2 <= o.conv_tol || nmv >= max_iter) break;
+    if (mv_prec != B2_FP64)
+      B2_REQUIRE(c->take_status() == 0, B2_ETIMEOUT, "tensor-core wait ran out");
+    if (res.resid2 <= tol || nmv >= max_iter) break;
     if (k >= kmax) {   // restart from the Ritz vector
       B2_CUDA(cudaMemcpyAsync(Vp, u.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
       B2_CUDA(cudaMemcpyAsync(Wp, hu.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -135,7 +144,7 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
     double* wk = Wp + int64_t(k) * n;
     B2_CUDA(cudaMemcpyAsync(vk, tp, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     b2k::launch_scale_inv_sqrt(vk, n, scal + 1, c->stream);
-    heff_apply(env, site, vk, wk, 0.0, &fl);
+    heff_apply(env, site, vk, wk, 0.0, &fl, mv_prec);
     res.flops += fl;
     ++nmv;
     // VW[j][k] = V_j . W_k (j <= k), VW[k][j] = V_k . W_j (j < k)
@@ -150,6 +159,60 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
   res.n_matvec = nmv;
   sync(c);
   return res;
+}
+
+// Davidson for H_eff.  FP64: the textbook iteration.  Split precision (mixed-precision
+// refinement): each round forms one FP64 product w = H u of the current unit vector u,
+// the FP64 Rayleigh quotient theta = u.w and residual r = w - theta u; it stops when
+// |r|^2 <= conv_tol.  Otherwise a Davidson solve seeded with the exact pair (u, w) runs with
+// split-precision products until its own residual drops by 1e-4 relative to |r|^2 (or
+// conv_tol) or 12 products, and its Ritz vector becomes the next u.  The returned energy
+// and residual are the FP64 ones of the returned vector.
+DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o) {
+  if (o.prec == B2_FP64) return davidson_core(env, site, psi, o, B2_FP64, nullptr, o.conv_tol);
+  B2_REQUIRE(o.prec == B2_BF16X3, B2_EUNSUPPORTED, "precision not implemented in this build");
+  Ctx* c = env->ctx;
+  WindowProgram& wp = window_program(env, site);
+  const int64_t n = wp.psi.size;
+  const int rounds = o.refine_max > 0 ? o.refine_max : 8;
+  const int max_total = o.max_iter > 0 ? o.max_iter : 30;
+  DevBuf w(c, sizeof(double) * n), sc(c, sizeof(double) * (256 * 16 + 8));
+  double* part = sc.as<double>();
+  double* s = part + 256 * 16;
+  DavidsonResult total;
+  double fl = 0;
+  // normalise the guess
+  b2k::launch_multidot(1, psi, n, psi, n, part, s, 1, c->stream);
+  b2k::launch_scale_inv_sqrt(psi, n, s, c->stream);
+  for (int round = 0;; ++round) {
+    heff_apply(env, site, psi, w.as<double>(), 0.0, &fl, B2_FP64);
+    total.flops += fl;
+    total.n_matvec += 1;
+    b2k::launch_multidot(1, psi, n, w.as<double>(), n, part, s + 1, 1, c->stream);   // theta
+    double th = 0;
+    B2_CUDA(cudaMemcpyAsync(&th, s + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    // r = w - theta u into the scratch of the inner solve's first correction
+    DevBuf r(c, sizeof(double) * n);
+    B2_CUDA(cudaMemcpyAsync(r.ptr, w.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    b2k::launch_axpby(r.as<double>(), psi, n, 1.0, -th, c->stream);
+    b2k::launch_multidot(1, r.as<double>(), n, r.as<double>(), n, part, s + 2, 1, c->stream);
+    double r2 = 0;
+    B2_CUDA(cudaMemcpyAsync(&r2, s + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    total.energy = th;
+    total.resid2 = r2;
+    if (std::getenv("B2_TRACE_DAVIDSON"))
+      std::fprintf(stderr, "refine site %d round %d theta %.15f r2 %.3e\n", site, round, th, r2);
+    if (r2 <= o.conv_tol || round >= rounds || total.n_matvec >= max_total) break;
+    b2_dav_opts inner = o;
+    inner.max_iter = std::min(12, std::max(2, max_total - total.n_matvec));
+    DavidsonResult d = davidson_core(env, site, psi, inner, o.prec, w.as<double>(),
+                                     std::max(o.conv_tol, 1e-4 * r2));
+    total.flops += d.flops;
+    total.n_matvec += d.n_matvec;
+  }
+  return total;
 }
 
 // --------------------------------------------------------------- density matrices

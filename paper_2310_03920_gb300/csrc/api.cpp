@@ -83,6 +83,7 @@ void b2_destroy(b2_ctx ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->c.stream);
   ctx->c.prof_clear();
+  if (ctx->c.d_status) ctx->c.raw_free(ctx->c.d_status);
   delete ctx;
 }
 
@@ -233,11 +234,12 @@ int b2_heff_apply(b2_ctx ctx, b2_env env, int site, const double* psi, double* o
     check_env(ctx, env);
     B2_REQUIRE(psi && out, B2_EINVAL, "null vector");
     B2_REQUIRE(std::isfinite(e_shift), B2_EINVAL, "non-finite shift");
-    B2_REQUIRE(prec == B2_FP64, B2_EUNSUPPORTED, "only B2_FP64 in this build");
+    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3, B2_EUNSUPPORTED,
+               "precision not implemented in this build (B2_FP64, B2_BF16X3 are)");
     ensure_device(ctx);
     auto& wp = b2::window_program(env, site);
     B2_REQUIRE(!overlap(psi, out, wp.psi.size), B2_EINVAL, "psi and out overlap");
-    b2::heff_apply(env, site, psi, out, e_shift, algo_flops);
+    b2::heff_apply(env, site, psi, out, e_shift, algo_flops, prec);
   });
 }
 

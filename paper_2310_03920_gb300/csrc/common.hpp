@@ -59,6 +59,10 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   void* raw_alloc(size_t bytes);
   void raw_free(void* p);
+  // device status word of bounded waits: allocated and zeroed on first use
+  int* status();
+  // read (synchronising the stream) and clear the status word; nonzero = a wait ran out
+  int take_status();
   void prof_clear() {
     for (auto& e : prof_events) {
       cudaEventDestroy(e.first);

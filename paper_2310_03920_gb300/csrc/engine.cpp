@@ -49,9 +49,10 @@ void GemmProgram::add_term(int out, const GemmTerm& t) {
     flops += 2.0 * o.M * t.K1 * t.K2 + 2.0 * o.M * double(t.K2) * o.N;
 }
 
-void GemmProgram::finalize(Ctx* c) {
+void GemmProgram::finalize(Ctx* c, bool with_tc) {
   terms.clear();
   tiles.clear();
+  tiles_tc.clear();
   for (size_t i = 0; i < outs.size(); ++i) {
     auto& o = outs[i];
     o.t0 = int(terms.size());
@@ -61,6 +62,9 @@ void GemmProgram::finalize(Ctx* c) {
     if (o.accumulate && o.t0 == o.t1) continue;
     for (int r = 0; r < o.M; r += b2k::kTile)
       for (int cc = 0; cc < o.N; cc += b2k::kTile) tiles.push_back({int(i), r, cc});
+    if (with_tc)
+      for (int r = 0; r < o.M; r += b2k::kTcTile)
+        for (int cc = 0; cc < o.N; cc += b2k::kTcTile) tiles_tc.push_back({int(i), r, cc});
   }
   B2_REQUIRE(terms.size() < (1u << 31), B2_EUNSUPPORTED, "too many contraction terms");
   by_out.clear();
@@ -68,11 +72,20 @@ void GemmProgram::finalize(Ctx* c) {
   upload(c, d_terms, terms);
   upload(c, d_outs, outs);
   upload(c, d_tiles, tiles);
+  if (with_tc) upload(c, d_tiles_tc, tiles_tc);
 }
 
 void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
   b2k::launch_gemm(d_tiles.as<b2k::GemmTile>(), int(tiles.size()), d_outs.as<b2k::GemmOut>(),
                    d_terms.as<GemmTerm>(), bt, c->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+void GemmProgram::launch_tc(Ctx* c, const BufTable& bt) const {
+  B2_REQUIRE(d_tiles_tc.ptr != nullptr || tiles_tc.empty(), B2_EINVAL,
+             "internal: program finalized without tensor-core tiles");
+  b2k::launch_gemm_tc(d_tiles_tc.as<b2k::GemmTile>(), int(tiles_tc.size()), d_outs.as<b2k::GemmOut>(),
+                      d_terms.as<GemmTerm>(), bt, c->status(), c->stream);
   B2_CUDA(cudaGetLastError());
 }
 
@@ -495,7 +508,7 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
       prog.add_term(ob, t);
     }
   }
-  prog.finalize(c);
+  prog.finalize(c, true);   // FP64 and tensor-core tilings
   int64_t comb_size = combL.size + combR.size;
   if (comb_size > 0) {
     wp.comb_buf.reset(c, size_t(comb_size) * sizeof(double));
@@ -541,7 +554,7 @@ WindowProgram& window_program(b2_env_s* env, int site) {
 }
 
 void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
-                double* flops) {
+                double* flops, b2_prec prec) {
   WindowProgram& wp = window_program(env, site);
   Ctx* c = env->ctx;
   BufTable bt{};
@@ -559,12 +572,17 @@ void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double 
     B2_CUDA(cudaEventCreate(&e0));
     B2_CUDA(cudaEventCreate(&e1));
     B2_CUDA(cudaEventRecord(e0, c->stream));
-    wp.heff.launch(c, bt);
+    if (prec == B2_FP64)
+      wp.heff.launch(c, bt);
+    else
+      wp.heff.launch_tc(c, bt);
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->prof_events.push_back({e0, e1});
     c->prof_flops += wp.heff.flops;
-  } else {
+  } else if (prec == B2_FP64) {
     wp.heff.launch(c, bt);
+  } else {
+    wp.heff.launch_tc(c, bt);
   }
   if (e_shift != 0.0) b2k::launch_axpby(out, psi, wp.psi.size, 1.0, -e_shift, c->stream);
   if (flops) *flops = wp.heff.flops;

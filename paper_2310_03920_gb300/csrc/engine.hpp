@@ -13,13 +13,14 @@ struct GemmProgram {
   std::vector<std::vector<b2k::GemmTerm>> by_out;
   std::vector<b2k::GemmOut> outs;
   std::vector<b2k::GemmTerm> terms;
-  std::vector<b2k::GemmTile> tiles;
-  DevBuf d_terms, d_outs, d_tiles;
+  std::vector<b2k::GemmTile> tiles, tiles_tc;   // 32x32 FP64 tiles, 128x128 tensor-core tiles
+  DevBuf d_terms, d_outs, d_tiles, d_tiles_tc;
   double flops = 0;
   int add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate);
   void add_term(int out, const b2k::GemmTerm& t);
-  void finalize(Ctx* c);
+  void finalize(Ctx* c, bool with_tc = false);
   void launch(Ctx* c, const b2k::BufTable& bt) const;
+  void launch_tc(Ctx* c, const b2k::BufTable& bt) const;
   bool empty() const { return tiles.empty(); }
 };
 
@@ -92,6 +93,6 @@ WindowProgram& window_program(b2_env_s* env, int site);
 void env_update_left(b2_env_s* env, int site);
 void env_update_right(b2_env_s* env, int site);
 void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
-                double* flops);
+                double* flops, b2_prec prec = B2_FP64);
 void heff_diag(b2_env_s* env, int site, double* diag);
 }  // namespace b2

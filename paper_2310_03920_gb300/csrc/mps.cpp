@@ -30,6 +30,23 @@ void Ctx::raw_free(void* p) {
     cudaFreeAsync(p, stream);
 }
 
+int* Ctx::status() {
+  if (!d_status) {
+    d_status = static_cast<int*>(raw_alloc(256));
+    B2_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+  }
+  return d_status;
+}
+
+int Ctx::take_status() {
+  if (!d_status) return 0;
+  int h = 0;
+  B2_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  B2_CUDA(cudaStreamSynchronize(stream));
+  if (h) B2_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+  return h;
+}
+
 void SiteTensor::build(const Bond& left, const Bond& right) {
   blocks.clear();
   lookup.assign(size_t(left.size()) * 4, -1);

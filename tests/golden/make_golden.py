@@ -7,7 +7,7 @@ Cases:
                     M = 64, 6 sweeps
   hubbard_L12_M48   Hubbard open chain L = 12, t = 1, U = 4, half filling, MPS seed 112,
                     M = 48, 4 sweeps
-Davidson: |r|^2 <= 1e-10 with up to 200 products and a 40-vector subspace, so that every
+Davidson: |r|^2 <= 1e-12 with up to 200 products and a 40-vector subspace, so that every
 solve converges (a solve stopped early depends on rounding, which differs between any two
 implementations).
 """
@@ -24,9 +24,9 @@ from synth import (config_integrals, hubbard_integrals, occupancies, random_mps,
                    sector_sizes)
 
 CASES = {
-    "abinitio_n8_M64": dict(ints="abinitio_n8", M=64, sweeps=6, mps_seed=100, max_iter=200,
+    "abinitio_n8_M64": dict(ints="abinitio_n8", M=64, sweeps=6, mps_seed=100, max_iter=200, tol=1e-12,
                             max_sub=40),
-    "hubbard_L12_M48": dict(ints=("hubbard", 12, 1.0, 4.0), M=48, sweeps=4, mps_seed=112,
+    "hubbard_L12_M48": dict(ints=("hubbard", 12, 1.0, 4.0), M=48, sweeps=4, mps_seed=112, tol=1e-12,
                             max_iter=200, max_sub=40),
 }
 
@@ -51,7 +51,7 @@ def main():
         h, eri, N, tsz, bonds, sites, c = case_inputs(name)
         t0 = time.time()
         d = dmrg.DMRG(mpo.MPO(h, eri), bonds, sites)
-        es = d.run([c["M"]] * c["sweeps"], max_iter=c["max_iter"], max_sub=c["max_sub"])
+        es = d.run([c["M"]] * c["sweeps"], tol=c["tol"], max_iter=c["max_iter"], max_sub=c["max_sub"])
         rec = {"sweep_energies": es, "n_matvec": sum(s["n_matvec"] for s in d.stats),
                "seconds": time.time() - t0}
         if h.shape[0] <= 12:

@@ -185,7 +185,7 @@ def test_sweep_energies_match_oracle(ctx, case):
     m = b2.b2_build_mpo(ctx, h, eri, 0.0, N, tsz)
     s = b2.b2_mps_import(ctx, bonds, sites, N, tsz, center=0)
     env = b2.b2_env_init(ctx, m, s, center=0)
-    res = b2.b2_sweep(ctx, m, s, env, [c["M"]] * c["sweeps"], dav_max_iter=c["max_iter"],
+    res = b2.b2_sweep(ctx, m, s, env, [c["M"]] * c["sweeps"], conv_tol=c["tol"], dav_max_iter=c["max_iter"],
                       max_subspace=c["max_sub"])
     es = [r["energy"] for r in res]
     for e, g in zip(es, gold["sweep_energies"]):
