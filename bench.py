@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     return ap.parse_args()
 
@@ -256,7 +257,7 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    energies, flops, step_ms = [], 0.0, []
+    energies, flops, step_ms, breakdown = [], 0.0, [], []
     b2.b2_profile(ctx, True)
     barrier()
     with ClockSampler(local) as clk:
@@ -270,6 +271,8 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             energies.append(res[0]["energy"])
             flops += res[0]["matvec_flops"]
+            breakdown.append({k: res[0][k] for k in ("t_davidson", "t_split", "n_matvec",
+                                                     "discarded_weight", "max_bond")})
     barrier()
     prof = b2.b2_profile_read(ctx)
     b2.b2_profile(ctx, False)
@@ -288,8 +291,8 @@ def main():
     # e2e through the public API from host buffers: import, env, one sweep, export
     bonds_now, sites_now, _ = b2.b2_mps_export(ctx, mps_h)
     h2d = sum(b.nbytes for blocks in sites_now for b in blocks.values())
-    e2e_ms, e2e_flops = [], 0.0
-    for _ in range(max(1, min(args.steps, 2))):
+    e2e_ms, e2e_flops, d2h = [], 0.0, 0
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -303,7 +306,7 @@ def main():
         d2h = sum(b.nbytes for blocks in out[1] for b in blocks.values())
         b2.b2_free_env(en2)
         b2.b2_free_mps(s2)
-    e2e_val = e2e_flops / (sum(e2e_ms) * 1e-3) / 1e12
+    e2e_val = e2e_flops / (sum(e2e_ms) * 1e-3) / 1e12 if e2e_ms else None
 
     if rank != 0:
         return
@@ -325,10 +328,11 @@ def main():
                        "n_elec": L, "two_sz": 0, "M": M, "prec": args.prec,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "sweep_energy": energies[-1], "sweep_ms": step_ms,
+            "sweep_energy": energies[-1], "sweep_ms": step_ms, "sweep_breakdown": breakdown,
             "roofline": roofline, "gpu_launches": int(prof["launches"]),
             "clocks": clk.summary(),
-            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": statistics.mean(e2e_ms),
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s",
+                    "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     if not args.no_cpu_baseline and world == 1:
         budget = args.cpu_budget

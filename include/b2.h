@@ -204,6 +204,8 @@ typedef struct {
   double other_flops;         /* algorithmic flops of environment updates and splits */
   int n_matvec;
   int max_bond;               /* largest bond dimension after the sweep */
+  double t_davidson;          /* wall time in the Davidson solves */
+  double t_split;             /* wall time in truncation, environment update and guess */
 } b2_sweep_result;
 int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts* opts,
              b2_sweep_result* per_sweep);
@@ -217,6 +219,7 @@ int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts
  *   evecs    device, sum dims^2 FP64: row-major, column t is the eigenvector of evals[t] */
 int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, double* evals,
                     double* evecs);
+
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every

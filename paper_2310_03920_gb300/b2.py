@@ -40,7 +40,8 @@ class SweepOpts(ctypes.Structure):
 
 class SweepResult(ctypes.Structure):
     _fields_ = [("energy", _d), ("discarded_weight", _d), ("seconds", _d), ("matvec_flops", _d),
-                ("other_flops", _d), ("n_matvec", _i), ("max_bond", _i)]
+                ("other_flops", _d), ("n_matvec", _i), ("max_bond", _i), ("t_davidson", _d),
+                ("t_split", _d)]
 
 
 class ProfileData(ctypes.Structure):

@@ -655,23 +655,33 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
     B2_REQUIRE(M >= 1, B2_EINVAL, "bond dimension must be positive");
     b2_sweep_result r{};
     double dw = 0, e = 0;
-    for (int i = 0; i <= n - 2; ++i) {
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto secs = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double>(b - a).count();
+    };
+    auto solve = [&](int i) {
+      auto ta = now();
       DavidsonResult d = davidson(env, i, psi.as<double>(), dop);
+      r.t_davidson += secs(ta, now());
       r.matvec_flops += d.flops;
       r.n_matvec += d.n_matvec;
       e = d.energy;
+    };
+    for (int i = 0; i <= n - 2; ++i) {
+      solve(i);
       if (i < n - 2) {
+        auto ta = now();
         split_left(env, i, psi, M, cutoff, &dw, &r.other_flops);
+        r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
     }
     for (int i = n - 2; i >= 0; --i) {
-      DavidsonResult d = davidson(env, i, psi.as<double>(), dop);
-      r.matvec_flops += d.flops;
-      r.n_matvec += d.n_matvec;
-      e = d.energy;
+      solve(i);
       if (i > 0) {
+        auto ta = now();
         split_right(env, i, psi, M, cutoff, &dw, &r.other_flops, true);
+        r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
     }
