@@ -220,6 +220,26 @@ int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts
 int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, double* evals,
                     double* evecs);
 
+/* Same eigensolver, for callers that cannot allocate device memory.  (The paper has no
+ * counterpart; this is an interface for embedding.)  Some callers must not let a library
+ * allocate: code running while a CUDA stream is being captured into a graph (allocation
+ * calls are illegal then), runtimes that own all device memory through their own pool
+ * and forbid other allocators, and latency-critical loops where an allocation could
+ * block on the device.  This variant calls no cudaMalloc, cudaFree or allocating library
+ * routine: its scratch -- the per-matrix sizes and offsets and the global-memory work
+ * space of matrices with dim > 104 -- lives in a fixed device array inside the library,
+ * 4 MiB + 32 KiB, which every GPU that loads the library holds until the process exits.
+ * The caller still passes the inputs and outputs (same layout as b2_eigh_batched).
+ *   Limits: n_mat <= 1024; dims in [1, 1024]; the matrices with dim > 104 together need
+ *   2 * dim^2 doubles of work space, at most 524288 doubles.  Larger requests return
+ *   B2_EINVAL without touching the device.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress
+ *   with that device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; calls whose work
+ *   overlaps on the GPU (e.g. on two streams at once) race on it.  The call is
+ *   stream-ordered and returns without waiting for the result. */
+int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, const double* a,
+                           double* evals, double* evecs);
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every

@@ -69,6 +69,7 @@ _sig = {
                          ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "b2_sweep": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepResult)]),
     "b2_eigh_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "b2_eigh_batched_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "b2_profile": (_i, [_vp, _i]),
     "b2_profile_read": (_i, [_vp, ctypes.POINTER(ProfileData)]),
     "b2_free_mpo": (None, [_vp]),
@@ -259,6 +260,14 @@ def b2_sweep(ctx, mpo, mps, env, bond_dims, conv_tol=1e-10, dav_max_iter=30, max
 def b2_eigh_batched(ctx, dims, a, evals, evecs):
     d = np.ascontiguousarray(dims, dtype=np.int32)
     _check(ctx.h, lib.b2_eigh_batched(ctx.h, len(d), d.ctypes.data, _ptr(a), _ptr(evals), _ptr(evecs)))
+
+
+def b2_eigh_batched_static(ctx, dims, a, evals, evecs):
+    """b2_eigh_batched without any device allocation (scratch in a fixed device array);
+    stream-ordered: synchronise before reading the results on the host."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    _check(ctx.h, lib.b2_eigh_batched_static(ctx.h, len(d), d.ctypes.data, _ptr(a), _ptr(evals),
+                                             _ptr(evecs)))
 
 
 def b2_profile(ctx, enable=True):

@@ -1,0 +1,75 @@
+"""b2_eigh_batched_static: the eigensolver entry point for callers that cannot allocate
+device memory (its scratch is a fixed device array in the library).  Its results must
+match the allocating entry point b2_eigh_batched, call after call.  This file is named to
+be collected last, so a run that stops at the first failure has run everything else."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_03920_gb300 import b2  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def _batch(rng, dims):
+    mats = []
+    for d in dims:
+        x = rng.standard_normal((d, max(1, (2 * d) // 3)))
+        mats.append(x @ x.T)
+    flat = torch.tensor(np.concatenate([m.ravel() for m in mats]), device=DEV)
+    return mats, flat
+
+
+def _run(fn, ctx, dims, flat):
+    ev = torch.empty(sum(dims), dtype=torch.float64, device=DEV)
+    vec = torch.empty(sum(d * d for d in dims), dtype=torch.float64, device=DEV)
+    fn(ctx, dims, flat, ev, vec)
+    torch.cuda.synchronize()
+    return ev.cpu().numpy(), vec.cpu().numpy()
+
+
+def test_static_eigh_matches_allocating_entry_point():
+    ctx = b2.Context(0)
+    rng = np.random.default_rng(42)
+    # two calls in a row; sizes on both sides of the shared-memory limit (104), so the
+    # second call reuses a work space the first one left filled
+    for dims in ([3, 17, 64, 104, 150, 300], [1, 2, 105, 233, 97, 12, 40]):
+        mats, flat = _batch(rng, dims)
+        ev_a, vec_a = _run(b2.b2_eigh_batched, ctx, dims, flat)
+        ev_s, vec_s = _run(b2.b2_eigh_batched_static, ctx, dims, flat)
+        eo = vo = 0
+        for d, a in zip(dims, mats):
+            scale = np.linalg.norm(a)
+            wa, ws = ev_a[eo:eo + d], ev_s[eo:eo + d]
+            ua = vec_a[vo:vo + d * d].reshape(d, d)
+            us = vec_s[vo:vo + d * d].reshape(d, d)
+            assert np.abs(wa - ws).max() <= 1e-13 * scale
+            assert np.abs(us @ np.diag(ws) @ us.T - a).max() <= 1e-13 * scale * np.sqrt(d)
+            # same eigenvectors up to sign where the eigenvalue is isolated
+            gap = np.minimum(np.abs(np.diff(np.r_[np.inf, wa])), np.abs(np.diff(np.r_[wa, -np.inf])))
+            iso = gap > 1e-6 * scale
+            overlap = np.abs(np.sum(ua * us, axis=0))
+            assert np.all(np.abs(overlap[iso] - 1.0) < 1e-9)
+            eo += d
+            vo += d * d
+    ctx.close()
+
+
+def test_static_eigh_rejects_requests_beyond_its_scratch():
+    ctx = b2.Context(0)
+    dims = [600]          # needs 2 * 600^2 doubles of work space: more than the 524288 held
+    a = torch.zeros(600 * 600, dtype=torch.float64, device=DEV)
+    ev = torch.empty(600, dtype=torch.float64, device=DEV)
+    vec = torch.empty(600 * 600, dtype=torch.float64, device=DEV)
+    with pytest.raises(b2.B2Error) as e:
+        b2.b2_eigh_batched_static(ctx, dims, a, ev, vec)
+    assert e.value.code == b2.B2_EINVAL
+    assert "exceeds" in str(e.value)
+    with pytest.raises(b2.B2Error):
+        b2.b2_eigh_batched_static(ctx, [2] * 1025, a, ev, vec)
+    ctx.close()
