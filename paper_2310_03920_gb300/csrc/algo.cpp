@@ -20,6 +20,30 @@ using b2k::kTwoOp;
 
 static void sync(Ctx* c) { B2_CUDA(cudaStreamSynchronize(c->stream)); }
 
+// Phase timing for diagnosis: with B2_TRACE_TIME set, each mark synchronises the stream
+// and prints the wall time since the previous mark.
+struct Tracer {
+  Ctx* c;
+  const char* name;
+  int site;
+  bool on;
+  std::chrono::steady_clock::time_point t;
+  Tracer(Ctx* c_, const char* n, int s) : c(c_), name(n), site(s), on(std::getenv("B2_TRACE_TIME")) {
+    if (on) {
+      sync(c);
+      t = std::chrono::steady_clock::now();
+    }
+  }
+  void mark(const char* what) {
+    if (!on) return;
+    sync(c);
+    auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "trace %s %d %s %.3f ms\n", name, site, what,
+                 std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 // ------------------------------------------------------------ two-site contraction
 // out(jl, s1, s2) = sum_jm X(jl, s1 -> jm) Y(jm, s2 -> jr) for a psi layout on bonds (a, c);
 // X on bonds (a, b), Y on bonds (b, c).
@@ -280,6 +304,7 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
 void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
                 double* flops) {
   Ctx* c = env->ctx;
+  Tracer tr(c, "split_left", i);
   b2_mps_s* mps = env->mps;
   WindowProgram& wp = window_program(env, i);
   const PsiLayout lay = wp.psi;
@@ -350,7 +375,9 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   bt.p[1] = rho.as<double>();
   prog.launch(c, bt);
   *flops += prog.flops;
+  tr.mark("rho");
   std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded);
+  tr.mark("eig+select");
 
   // new bond i+1 and A_i
   Bond nb;
@@ -435,7 +462,9 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   mps->bonds[i + 1] = nb;
   mps->sites[i] = std::move(A);
   env->R[i + 1].valid = false;
+  tr.mark("site+C");
   env_update_left(env, i);
+  tr.mark("env");
   // guess for window i+1: C . B_{i+2}
   if (i + 2 < mps->n) {
     PsiLayout nl;
@@ -454,6 +483,7 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
 void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
                  double* flops, bool make_guess) {
   Ctx* c = env->ctx;
+  Tracer tr(c, "split_right", i);
   b2_mps_s* mps = env->mps;
   WindowProgram& wp = window_program(env, i);
   const PsiLayout lay = wp.psi;
@@ -528,7 +558,9 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   bt.p[1] = rho.as<double>();
   prog.launch(c, bt);
   *flops += prog.flops;
+  tr.mark("rho");
   std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded);
+  tr.mark("eig+select");
 
   Bond nb;
   std::vector<int> new_idx(secs.size(), -1);
@@ -608,7 +640,9 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   mps->bonds[i + 1] = nb;
   mps->sites[i + 1] = std::move(Bt);
   env->L[i + 1].valid = false;
+  tr.mark("site+C");
   env_update_right(env, i + 1);
+  tr.mark("env");
   if (make_guess && i > 0) {
     PsiLayout nl;
     nl.build(mps->bonds[i - 1], mps->bonds[i + 1]);
