@@ -227,10 +227,10 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
  * and forbid other allocators, and latency-critical loops where an allocation could
  * block on the device.  This variant calls no cudaMalloc, cudaFree or allocating library
  * routine: its scratch -- the per-matrix sizes and offsets and the global-memory work
- * space of matrices with dim > 104 -- lives in a fixed device array inside the library,
+ * space of matrices with dim > 112 -- lives in a fixed device array inside the library,
  * 4 MiB + 32 KiB, which every GPU that loads the library holds until the process exits.
  * The caller still passes the inputs and outputs (same layout as b2_eigh_batched).
- *   Limits: n_mat <= 1024; dims in [1, 1024]; the matrices with dim > 104 together need
+ *   Limits: n_mat <= 1024; dims in [1, 1024]; the matrices with dim > 112 together need
  *   2 * dim^2 doubles of work space, at most 524288 doubles.  Larger requests return
  *   B2_EINVAL without touching the device.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress

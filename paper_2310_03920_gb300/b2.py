@@ -201,6 +201,15 @@ def b2_mps_export(ctx, mps):
     return bonds, sites, center.value
 
 
+def b2_mps_random(ctx, mpo, bond_dim, occ=None, seed=0):
+    out = _vp()
+    occ_arr = None if occ is None else np.ascontiguousarray(occ, dtype=np.float64)
+    _check(ctx.h, lib.b2_mps_random(ctx.h, mpo, bond_dim,
+                                    None if occ_arr is None else occ_arr.ctypes.data,
+                                    ctypes.c_uint64(seed), ctypes.byref(out)))
+    return out
+
+
 def b2_env_init(ctx, mpo, mps, center=0):
     out = _vp()
     _check(ctx.h, lib.b2_env_init(ctx.h, mpo, mps, center, ctypes.byref(out)))

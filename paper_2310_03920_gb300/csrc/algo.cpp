@@ -190,16 +190,17 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
 // the FP64 Rayleigh quotient theta = u.w and residual r = w - theta u; it stops when
 // |r|^2 <= conv_tol.  Otherwise a Davidson solve seeded with the exact pair (u, w) runs with
 // split-precision products until its own residual drops by 1e-4 relative to |r|^2 (or
-// conv_tol) or 12 products, and its Ritz vector becomes the next u.  The returned energy
-// and residual are the FP64 ones of the returned vector.
+// conv_tol) or max_iter products, and its Ritz vector becomes the next u.  At most
+// refine_max (default 4) rounds.  The returned energy and residual are the FP64 ones of
+// the returned vector.
 DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o) {
   if (o.prec == B2_FP64) return davidson_core(env, site, psi, o, B2_FP64, nullptr, o.conv_tol);
   B2_REQUIRE(o.prec == B2_BF16X3, B2_EUNSUPPORTED, "precision not implemented in this build");
   Ctx* c = env->ctx;
   WindowProgram& wp = window_program(env, site);
   const int64_t n = wp.psi.size;
-  const int rounds = o.refine_max > 0 ? o.refine_max : 8;
-  const int max_total = o.max_iter > 0 ? o.max_iter : 30;
+  const int rounds = o.refine_max > 0 ? o.refine_max : 4;
+  const int max_inner = o.max_iter > 0 ? o.max_iter : 30;
   DevBuf w(c, sizeof(double) * n), sc(c, sizeof(double) * (256 * 16 + 8));
   double* part = sc.as<double>();
   double* s = part + 256 * 16;
@@ -228,9 +229,9 @@ DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts&
     total.resid2 = r2;
     if (std::getenv("B2_TRACE_DAVIDSON"))
       std::fprintf(stderr, "refine site %d round %d theta %.15f r2 %.3e\n", site, round, th, r2);
-    if (r2 <= o.conv_tol || round >= rounds || total.n_matvec >= max_total) break;
+    if (r2 <= o.conv_tol || round >= rounds) break;
     b2_dav_opts inner = o;
-    inner.max_iter = std::min(12, std::max(2, max_total - total.n_matvec));
+    inner.max_iter = max_inner;
     DavidsonResult d = davidson_core(env, site, psi, inner, o.prec, w.as<double>(),
                                      std::max(o.conv_tol, 1e-4 * r2));
     total.flops += d.flops;
@@ -267,7 +268,7 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     eoffs[j] = secs[j].eoff;
     tot_e += dims[j];
     max_dim = std::max(max_dim, dims[j]);
-    if (dims[j] > 104) {
+    if (dims[j] > b2k::kJacobiSmemAV) {
       woffs[j] = tot_w;
       tot_w += 2 * int64_t(dims[j]) * dims[j];
     }

@@ -374,38 +374,52 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
   wp.ver_r = R.version;
   wp.psi.build(bl, br);
 
-  // two-site operators O_ab[u, v], u = 4 s1' + s2', v = 4 s1 + s2, with the sign of
-  // moving the site-(i+1) operator past s1 and the right part past s1 s2 folded in
+  // Two-site operator entries grouped by local pattern (u, v), u = 4 s1' + s2',
+  // v = 4 s1 + s2: sum over w' of W_i[a,w']_{s1's1} W_{i+1}[w',b]_{s2's2}, with the sign of
+  // moving the site-(i+1) operator past s1 and the right part past s1 s2 folded in.  Flat
+  // edge lists per pattern; duplicates (several w' joining the same a, b) are merged after
+  // a stable sort, so they are summed in generation order.
   std::vector<std::vector<int>> byw(mpo->D[i + 1]);
   for (size_t e = 0; e < mpo->W[i + 1].size(); ++e) byw[mpo->W[i + 1][e].w].push_back(int(e));
-  std::map<std::pair<int, int>, std::map<int, double>> O;
+  std::vector<std::vector<Edge>> pat(256);
   for (const auto& e1 : mpo->W[i]) {
+    int nz1[16], n1 = 0;
+    for (int a1 = 0; a1 < 16; ++a1)
+      if (e1.m[a1] != 0) nz1[n1++] = a1;
     for (int e2i : byw[e1.w2]) {
       const auto& e2 = mpo->W[i + 1][e2i];
-      int p2 = op_parity(e2.m);
-      int pb = mpo->parity[i + 2][e2.w2];
-      auto& dst = O[{e1.w, e2.w2}];
-      for (int a1 = 0; a1 < 16; ++a1) {
-        double x1 = e1.m[a1];
-        if (x1 == 0) continue;
-        int s1p = a1 / 4, s1 = a1 % 4;
+      const int p2 = op_parity(e2.m);
+      const int pb = mpo->parity[i + 2][e2.w2];
+      for (int k1 = 0; k1 < n1; ++k1) {
+        const int a1 = nz1[k1];
+        const double x1 = e1.m[a1];
+        const int s1p = a1 / 4, s1 = a1 % 4;
         for (int a2 = 0; a2 < 16; ++a2) {
-          double x2 = e2.m[a2];
+          const double x2 = e2.m[a2];
           if (x2 == 0) continue;
-          int s2p = a2 / 4, s2 = a2 % 4;
+          const int s2p = a2 / 4, s2 = a2 % 4;
           double sign = 1.0;
           if (p2 && par_n(kSiteN[s1])) sign = -sign;
           if (pb && par_n(kSiteN[s1] + kSiteN[s2])) sign = -sign;
-          dst[(s1p * 4 + s2p) * 16 + s1 * 4 + s2] += sign * x1 * x2;
+          pat[(s1p * 4 + s2p) * 16 + s1 * 4 + s2].push_back({e1.w, e2.w2, sign * x1 * x2});
         }
       }
     }
   }
-  // edges per local pattern (u, v)
-  std::map<int, std::vector<Edge>> pat;
-  for (auto& ab : O)
-    for (auto& uv : ab.second)
-      if (uv.second != 0) pat[uv.first].push_back({ab.first.first, ab.first.second, uv.second});
+  for (auto& edges : pat) {
+    std::stable_sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
+      return x.a != y.a ? x.a < y.a : x.b < y.b;
+    });
+    size_t w = 0;
+    for (size_t r = 0; r < edges.size();) {
+      Edge m = edges[r];
+      size_t q = r + 1;
+      while (q < edges.size() && edges[q].a == m.a && edges[q].b == m.b) m.v += edges[q++].v;
+      if (m.v != 0) edges[w++] = m;
+      r = q;
+    }
+    edges.resize(w);
+  }
 
   // outputs: every psi block, overwritten
   GemmProgram& prog = wp.heff;
@@ -418,41 +432,55 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     double coef;
   };
   std::vector<Pending> pending;
-  for (auto& pv : pat) {
-    int u = pv.first / 16, v = pv.first % 16;
-    auto& edges = pv.second;
+  const int Da = mpo->D[i], Db = mpo->D[i + 2];
+  std::vector<int> dega(Da, 0), degb(Db, 0), posa(Da, -1), posb(Db, -1);
+  for (int pv = 0; pv < 256; ++pv) {
+    auto& edges = pat[pv];
+    if (edges.empty()) continue;
+    const int u = pv / 16, v = pv % 16;
     // greedy vertex cover: highest degree first; each chosen vertex takes its remaining
     // edges as one group (the other side is precombined)
-    std::map<int, int> dega, degb;
+    std::vector<int> ta, tb;
     for (auto& e : edges) {
-      dega[e.a]++;
-      degb[e.b]++;
+      if (dega[e.a]++ == 0) ta.push_back(e.a);
+      if (degb[e.b]++ == 0) tb.push_back(e.b);
     }
+    // incidence: edges are sorted by a; by_b holds edge indices sorted by (b, a)
+    for (size_t k = 0; k < edges.size(); ++k)
+      if (posa[edges[k].a] < 0) posa[edges[k].a] = int(k);
+    std::vector<int> by_b(edges.size());
+    for (size_t k = 0; k < edges.size(); ++k) by_b[k] = int(k);
+    std::stable_sort(by_b.begin(), by_b.end(), [&](int x, int y) { return edges[x].b < edges[y].b; });
+    for (size_t k = 0; k < by_b.size(); ++k)
+      if (posb[edges[by_b[k]].b] < 0) posb[edges[by_b[k]].b] = int(k);
     struct Vert {
       int deg, side, id;
     };
     std::vector<Vert> verts;
-    for (auto& x : dega) verts.push_back({x.second, 0, x.first});
-    for (auto& x : degb) verts.push_back({x.second, 1, x.first});
-    std::stable_sort(verts.begin(), verts.end(), [](const Vert& x, const Vert& y) {
+    verts.reserve(ta.size() + tb.size());
+    for (int x : ta) verts.push_back({dega[x], 0, x});
+    for (int x : tb) verts.push_back({degb[x], 1, x});
+    std::sort(verts.begin(), verts.end(), [](const Vert& x, const Vert& y) {
       if (x.deg != y.deg) return x.deg > y.deg;
       if (x.side != y.side) return x.side < y.side;
       return x.id < y.id;
     });
-    std::map<int, std::vector<int>> inc_a, inc_b;
-    for (size_t k = 0; k < edges.size(); ++k) {
-      inc_a[edges[k].a].push_back(int(k));
-      inc_b[edges[k].b].push_back(int(k));
-    }
     std::vector<char> used(edges.size(), 0);
     for (auto& vt : verts) {
-      auto& inc = vt.side == 0 ? inc_a[vt.id] : inc_b[vt.id];
       std::vector<std::pair<int, double>> others;
-      for (int k : inc)
-        if (!used[k]) {
-          used[k] = 1;
-          others.push_back({vt.side == 0 ? edges[k].b : edges[k].a, edges[k].v});
-        }
+      if (vt.side == 0) {
+        for (int k = posa[vt.id]; k < int(edges.size()) && edges[k].a == vt.id; ++k)
+          if (!used[k]) {
+            used[k] = 1;
+            others.push_back({edges[k].b, edges[k].v});
+          }
+      } else {
+        for (int k = posb[vt.id]; k < int(by_b.size()) && edges[by_b[k]].b == vt.id; ++k)
+          if (!used[by_b[k]]) {
+            used[by_b[k]] = 1;
+            others.push_back({edges[by_b[k]].a, edges[by_b[k]].v});
+          }
+      }
       if (others.empty()) continue;
       Pending p;
       p.u = u;
@@ -469,6 +497,8 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
       p.coef = p.lop.coef * p.rop.coef;
       pending.push_back(std::move(p));
     }
+    for (int x : ta) dega[x] = 0, posa[x] = -1;
+    for (int x : tb) degb[x] = 0, posb[x] = -1;
   }
   // the R combinations live after the L ones in the same buffer
   int64_t shiftR = combL.size;
@@ -515,23 +545,22 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     cp.finalize(c);
   }
 
-  // diagonal: pairs whose channels keep the sector (diagonal blocks) and diagonal patterns
+  // diagonal: diagonal patterns whose channels keep the sector (dq = 0 on both sides)
+  std::vector<std::vector<Edge>> dedges(16);
+  for (int v = 0; v < 16; ++v)
+    for (const auto& e : pat[v * 16 + v])
+      if (mpo->dq[i][e.a] == QN{0, 0} && mpo->dq[i + 2][e.b] == QN{0, 0}) dedges[v].push_back(e);
   for (const auto& pb : wp.psi.blocks) {
     b2k::DiagOut d;
     d.off = pb.off;
     d.ml = pb.ml;
     d.mr = pb.mr;
     d.t0 = int(wp.diag_terms.size());
-    int v = pb.s1 * 4 + pb.s2;
-    for (auto& ab : O) {
-      auto it = ab.second.find(v * 16 + v);
-      if (it == ab.second.end() || it->second == 0) continue;
-      int a = ab.first.first, b = ab.first.second;
-      int lb = L.blk[a][pb.jl], rb = R.blk[b][pb.jr];
+    for (const auto& e : dedges[pb.s1 * 4 + pb.s2]) {
+      int lb = L.blk[e.a][pb.jl], rb = R.blk[e.b][pb.jr];
       if (lb < 0 || rb < 0) continue;
-      if (L.blocks[lb].jb != pb.jl || R.blocks[rb].jb != pb.jr) continue;
-      double sign = (mpo->parity[i][a] && par_n(bl.q[pb.jl].n)) ? -1.0 : 1.0;
-      wp.diag_terms.push_back({L.blocks[lb].off, R.blocks[rb].off, sign * it->second});
+      double sign = (mpo->parity[i][e.a] && par_n(bl.q[pb.jl].n)) ? -1.0 : 1.0;
+      wp.diag_terms.push_back({L.blocks[lb].off, R.blocks[rb].off, sign * e.v});
     }
     d.t1 = int(wp.diag_terms.size());
     wp.diag_outs.push_back(d);

@@ -209,44 +209,73 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 
 // ================================================================ batched Jacobi
 // Cyclic Jacobi for a real symmetric matrix (Golub & Van Loan, Matrix Computations,
-// Alg. 8.5.2 / 8.5.3 "sym.schur2" rotation; parallel round-robin ordering of the pivot
-// pairs so that each round's m/2 rotations touch disjoint rows and columns).  A rotation
-// is skipped when the off-diagonal element is negligible next to both diagonal entries
-// (100|a_pq| adds nothing to |a_pp| nor |a_qq|); the iteration stops after a sweep
-// without rotations (at most kMaxSweeps sweeps).
-constexpr int kJacobiSmemMax = 104;
-constexpr int kJacobiMaxDim = 1024;
+// Alg. 8.5.2 / 8.5.3 "sym.schur2" rotation), one CTA per matrix.  Each sweep visits every
+// pivot pair once in round-robin order, m/2 disjoint pairs per round, so one round applies
+// the block-diagonal rotation J (2 x 2 blocks on the pairs) as A <- J^T A J.  Element
+// blocks A[{p_i, q_i}][{p_j, q_j}] depend only on their own four entries, so a round is
+// one pass over the 2 x 2 blocks of the upper triangle (mirrored below), and the
+// eigenvector matrix is kept transposed (V^T) so that its rotations update two contiguous
+// rows.  A rotation is skipped when the off-diagonal element is negligible next to both
+// diagonal entries (100|a_pq| adds nothing to |a_pp| nor |a_qq|); the iteration stops after
+// a sweep without rotations (at most kMaxSweeps sweeps).  A lives in shared memory for
+// dim <= kJacobiSmemA, V^T too for dim <= kJacobiSmemAV; larger matrices use global work
+// space (2 dim^2 doubles).
+constexpr int kJacobiSmemA = 160;
 constexpr int kMaxSweeps = 60;
+constexpr int kJacobiThreads = 512;
 
-__global__ void __launch_bounds__(256) k_jacobi(const int* __restrict__ dims,
-                                                const int64_t* __restrict__ offs,
-                                                const int64_t* __restrict__ eoffs,
-                                                const double* __restrict__ a, double* evals,
-                                                double* evecs, double* work,
-                                                const int64_t* __restrict__ woffs) {
+// dynamic shared memory needed by a matrix of dimension m
+__host__ __device__ inline size_t jacobi_smem_bytes(int m) {
+  const int mp = m + (m & 1);
+  size_t aux = size_t(mp) * (2 * sizeof(int)) + size_t(mp / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+  size_t mat = 0;
+  if (m <= kJacobiSmemAV)
+    mat = 2 * size_t(m) * m * sizeof(double);
+  else if (m <= kJacobiSmemA)
+    mat = size_t(m) * m * sizeof(double);
+  return mat + aux;
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict__ dims,
+                                                           const int64_t* __restrict__ offs,
+                                                           const int64_t* __restrict__ eoffs,
+                                                           const double* __restrict__ a,
+                                                           double* evals, double* evecs,
+                                                           double* work,
+                                                           const int64_t* __restrict__ woffs) {
   extern __shared__ double smem[];
-  __shared__ int perm[kJacobiMaxDim], perm2[kJacobiMaxDim];
-  __shared__ double cs[kJacobiMaxDim / 2], sn[kJacobiMaxDim / 2];
-  __shared__ int pi_[kJacobiMaxDim / 2], qi_[kJacobiMaxDim / 2];
   __shared__ int nrot;
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int m = dims[b];
-  double *A, *V;
-  if (m <= kJacobiSmemMax) {
+  const int mp = m + (m & 1), half = mp / 2;
+  double *A, *Vt;
+  double* next = smem;
+  if (m <= kJacobiSmemAV) {
     A = smem;
-    V = smem + m * m;
+    Vt = smem + size_t(m) * m;
+    next = Vt + size_t(m) * m;
+  } else if (m <= kJacobiSmemA) {
+    A = smem;
+    Vt = work + woffs[b] + size_t(m) * m;
+    next = smem + size_t(m) * m;
   } else {
     A = work + woffs[b];
-    V = A + int64_t(m) * m;
+    Vt = A + size_t(m) * m;
   }
+  double* cs = next;
+  double* sn = cs + half;
+  int* pi_ = reinterpret_cast<int*>(sn + half);
+  int* qi_ = pi_ + half;
+  int* perm = qi_ + half;
+  int* perm2 = perm + mp;
   const double* src = a + offs[b];
   for (int e = tid; e < m * m; e += nt) {
     A[e] = src[e];
-    V[e] = (e / m == e % m) ? 1.0 : 0.0;
+    Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
   }
-  const int mp = m + (m & 1), half = mp / 2;
   for (int i = tid; i < mp; i += nt) perm[i] = i;
   __syncthreads();
+  const int nblk = half * (half + 1) / 2;   // upper-triangle 2x2 blocks (i <= j)
   for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
@@ -273,45 +302,56 @@ __global__ void __launch_bounds__(256) k_jacobi(const int* __restrict__ dims,
         }
         cs[i] = c;
         sn[i] = s;
-        pi_[i] = rot ? p : -1;
-        qi_[i] = q;
+        pi_[i] = p;
+        qi_[i] = (q < m) ? q : -1;   // -1: p is unpaired this round (odd dimension)
         if (rot) atomicAdd(&nrot, 1);
       }
       __syncthreads();
-      for (int e = tid; e < half * m; e += nt) {   // rows: A <- J^T A
-        int i = e / m, k = e % m, p = pi_[i];
-        if (p < 0) continue;
-        int q = qi_[i];
-        double c = cs[i], s = sn[i];
-        double apk = A[p * m + k], aqk = A[q * m + k];
-        A[p * m + k] = c * apk - s * aqk;
-        A[q * m + k] = s * apk + c * aqk;
-      }
-      __syncthreads();
-      for (int e = tid; e < half * m; e += nt) {   // columns: A <- A J, V <- V J
-        int i = e / m, k = e % m, p = pi_[i];
-        if (p < 0) continue;
-        int q = qi_[i];
-        double c = cs[i], s = sn[i];
-        double akp = A[k * m + p], akq = A[k * m + q];
-        A[k * m + p] = c * akp - s * akq;
-        A[k * m + q] = s * akp + c * akq;
-        double vkp = V[k * m + p], vkq = V[k * m + q];
-        V[k * m + p] = c * vkp - s * vkq;
-        V[k * m + q] = s * vkp + c * vkq;
-      }
-      __syncthreads();
-      for (int i = tid; i < half; i += nt) {
-        int p = pi_[i];
-        if (p >= 0) {
-          int q = qi_[i];
-          A[p * m + q] = 0.0;
-          A[q * m + p] = 0.0;
+      // A <- J^T A J, one 2x2 block (pair i rows, pair j columns) per work item, i <= j
+      for (int e = tid; e < nblk; e += nt) {
+        // unrank e -> (i, j), 0 <= i <= j < half, row-major over the upper triangle
+        int i = int((2.0 * half + 1.0 - sqrt((2.0 * half + 1.0) * (2.0 * half + 1.0) - 8.0 * e)) * 0.5);
+        while (i > 0 && i * half - i * (i - 1) / 2 > e) --i;
+        while ((i + 1) * half - (i + 1) * i / 2 <= e) ++i;
+        const int j = i + (e - (i * half - i * (i - 1) / 2));
+        const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
+        const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (q >= 0 && u >= 0) {
+          double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
+          // rows: [c -s; s c] applied on (p, q); columns likewise on (r, u)
+          double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
+          double b21 = si * app + ci * aqp, b22 = si * apq + ci * aqq;
+          double n11 = cj * b11 - sj * b12, n12 = sj * b11 + cj * b12;
+          double n21 = cj * b21 - sj * b22, n22 = sj * b21 + cj * b22;
+          if (i == j && si != 0.0) { n12 = 0.0; n21 = 0.0; }
+          A[p * m + r] = n11; A[p * m + u] = n12; A[q * m + r] = n21; A[q * m + u] = n22;
+          if (i != j) {
+            A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
+          }
+        } else if (q >= 0) {   // column pair j is a single index r
+          double ap = A[p * m + r], aq = A[q * m + r];
+          double np = ci * ap - si * aq, nq = si * ap + ci * aq;
+          A[p * m + r] = np; A[q * m + r] = nq;
+          if (i != j) { A[r * m + p] = np; A[r * m + q] = nq; }
+        } else if (u >= 0) {   // row pair i is a single index p
+          double ar = A[p * m + r], au = A[p * m + u];
+          double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
+          A[p * m + r] = nr; A[p * m + u] = nu;
+          if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
         }
       }
-      for (int i = tid; i < mp; i += nt) {   // round-robin: keep perm[0], rotate the rest
-        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
+      // V <- V J: rows p, q of V^T
+      for (int e = tid; e < half * m; e += nt) {
+        int i = e / m, k = e % m;
+        int p = pi_[i], q = qi_[i];
+        double c = cs[i], s = sn[i];
+        if (q < 0 || s == 0.0) continue;
+        double vp = Vt[p * m + k], vq = Vt[q * m + k];
+        Vt[p * m + k] = c * vp - s * vq;
+        Vt[q * m + k] = s * vp + c * vq;
       }
+      for (int i = tid; i < mp; i += nt)   // round-robin: keep perm[0], rotate the rest
+        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
       __syncthreads();
       for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
       __syncthreads();
@@ -330,7 +370,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const int* __restrict__ dims,
       rank += (dj > di) || (dj == di && j < i);
     }
     ev[rank] = di;
-    for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = V[k * m + i];
+    for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = Vt[i * m + k];
   }
 }
 
@@ -338,17 +378,15 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s) {
   if (n_mat <= 0) return;
-  int sm_dim = max_dim <= kJacobiSmemMax ? max_dim : 0;
-  size_t smem = size_t(2) * sm_dim * sm_dim * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * kJacobiSmemMax * kJacobiSmemMax * int(sizeof(double)));
-    attr = true;
+  // the largest per-matrix need over every dimension up to max_dim
+  size_t smem = 0;
+  for (int m = 1; m <= max_dim; ++m) smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    attr = smem;
   }
-  // matrices larger than the shared-memory limit work in global scratch (woffs)
-  if (max_dim > kJacobiSmemMax) smem = size_t(2) * kJacobiSmemMax * kJacobiSmemMax * sizeof(double);
-  k_jacobi<<<n_mat, 256, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs);
+  k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs);
   g_launches += 1;
 }
 
@@ -638,6 +676,26 @@ __global__ void k_symmetrize(int k, const double* vw, int kmax, double* g) {
 
 void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s) {
   k_symmetrize<<<1, 256, 0, s>>>(k, vw, kmax, g);
+  g_launches += 1;
+}
+
+}  // namespace b2k
+
+namespace b2k {
+
+__global__ void k_scale_cols(int m, const double* __restrict__ u, const double* __restrict__ lam,
+                             double power, double floor_, double* out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    int c = e % m;
+    out[e] = u[e] * pow(fmax(lam[c], floor_), power);
+  }
+}
+
+void launch_scale_cols(int m, const double* u, const double* lam, double power, double floor_,
+                       double* out, cudaStream_t s) {
+  int blocks = (m * m + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_scale_cols<<<blocks, 256, 0, s>>>(m, u, lam, power, floor_, out);
   g_launches += 1;
 }
 

@@ -91,8 +91,10 @@ void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const 
 void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
                  const double* R, double* diag, cudaStream_t s);
 void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s);
-// Batched symmetric eigensolver; offs/voffs: element offsets of each matrix (dims^2 each)
-// and of its eigenvalues; work: scratch (sum dims^2 * 2 doubles) used for dims > 112.
+// Batched symmetric eigensolver; offs/eoffs: element offsets of each matrix (dims^2 each)
+// and of its eigenvalues; work/woffs: global work space of 2 dims^2 doubles for each
+// matrix with dims > kJacobiSmemAV (the smaller ones work in shared memory).
+constexpr int kJacobiSmemAV = 112;
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s);
@@ -124,5 +126,8 @@ void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cud
 // Build the symmetric k x k Rayleigh matrix from the stored overlaps: g[i*k+j] =
 // 0.5 (VW[i][j] + VW[j][i]), VW row-major with stride kmax.
 void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s);
+// out[r][c] = u[r][c] * max(lam[c], floor)^power for an m x m row-major matrix.
+void launch_scale_cols(int m, const double* u, const double* lam, double power, double floor,
+                       double* out, cudaStream_t s);
 
 }  // namespace b2k

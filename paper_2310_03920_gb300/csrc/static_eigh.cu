@@ -18,7 +18,7 @@
 namespace {
 
 constexpr int kMaxMats = 1024;
-constexpr int kShmemDim = 104;                 // larger matrices need global work space
+constexpr int kShmemDim = b2k::kJacobiSmemAV;   // larger matrices need global work space
 constexpr int64_t kWorkDoubles = int64_t(1) << 19;   // 4 MiB of Jacobi work space
 constexpr int64_t kMetaDoubles = 4096;               // dims + three offset tables
 constexpr int64_t kScratchDoubles = kMetaDoubles + kWorkDoubles;
@@ -79,7 +79,7 @@ extern "C" int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, co
       max_dim = dims[i] > max_dim ? dims[i] : max_dim;
     }
     B2_REQUIRE(w <= kWorkDoubles, B2_EINVAL,
-               "matrices larger than 104 need 2*dim^2 doubles each of static work space; "
+               "matrices larger than 112 need 2*dim^2 doubles each of static work space; "
                "their sum exceeds the 524288 available (4 MiB)");
     if (n_mat == 0) return B2_OK;
     double* base = scratch_address(ctx->c.device);

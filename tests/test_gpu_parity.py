@@ -216,3 +216,30 @@ def test_sweep_exact_bond_dimension_reaches_fci(ctx):
     res = b2.b2_sweep(ctx, m, s, env, [M] * 3)
     assert abs(res[-1]["energy"] - e_fci) < 1e-9
     _free(m, s, env)
+
+
+@pytest.mark.parametrize("kind", ["ab_initio", "hubbard"])
+def test_mps_random_is_right_canonical_with_generator_sectors(ctx, kind):
+    n, M = 10, 60
+    if kind == "hubbard":
+        h, eri = hubbard_integrals(n, 1.0, 4.0)
+        occ = np.full(n, 0.5)
+    else:
+        h, eri = ab_initio_integrals(n, seed=3)
+        occ = None
+    m = b2.b2_build_mpo(ctx, h, eri, 0.0, n, 0)
+    s = b2.b2_mps_random(ctx, m, M, occ=occ, seed=7)
+    bonds, sites, center = b2.b2_mps_export(ctx, s)
+    assert center == 0
+    # same sector sizes as the seeded generator's recipe
+    assert bonds == sector_sizes(n, n, 0, M, occupancies(n, n, kind))
+    lab, A = dmrg.blocks_to_dense(bonds, sites)
+    for k in range(1, n):
+        B = A[k].reshape(A[k].shape[0], -1)
+        assert np.abs(B @ B.T - np.eye(B.shape[0])).max() < 1e-10
+    assert abs(np.sum(A[0] ** 2) - 1.0) < 1e-12
+    # the state is usable: environments and a sweep run from it
+    env = b2.b2_env_init(ctx, m, s, center=0)
+    res = b2.b2_sweep(ctx, m, s, env, [M], dav_max_iter=60, max_subspace=40)
+    assert np.isfinite(res[0]["energy"])
+    _free(m, s, env)

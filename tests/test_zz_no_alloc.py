@@ -36,9 +36,9 @@ def _run(fn, ctx, dims, flat):
 def test_static_eigh_matches_allocating_entry_point():
     ctx = b2.Context(0)
     rng = np.random.default_rng(42)
-    # two calls in a row; sizes on both sides of the shared-memory limit (104), so the
+    # two calls in a row; sizes on both sides of the shared-memory limit (112), so the
     # second call reuses a work space the first one left filled
-    for dims in ([3, 17, 64, 104, 150, 300], [1, 2, 105, 233, 97, 12, 40]):
+    for dims in ([3, 17, 64, 112, 150, 300], [1, 2, 113, 233, 97, 12, 40]):
         mats, flat = _batch(rng, dims)
         ev_a, vec_a = _run(b2.b2_eigh_batched, ctx, dims, flat)
         ev_s, vec_s = _run(b2.b2_eigh_batched_static, ctx, dims, flat)
