@@ -5,7 +5,7 @@ wavefunction lives on the product of the left block states, the d = 16 two-site 
 space and the right block states), with the standard Davidson solver (Sec. 2.1.3 (iv)
 names it; settings thrds = 1e-10 on the squared residual and dav_max_iter = 30 as in
 Listing 1), density-matrix truncation to M states per bond, and environments
-(renormalized operators) built from an MPO (Sec. 3.2).
+(renormalized operators) built from an MPO (Sec. 2.3).
 
 Representation (deliberately simple): every bond index runs over all its states in
 sector order, tensors are dense numpy arrays whose forbidden (quantum-number violating)
@@ -104,7 +104,7 @@ def two_site_operators(mpo, i):
 
 
 class Heff:
-    """H_eff of window (i, i+1) from L_i, R_{i+2} and the MPO (Sec. 2.1.2, Sec. 3.2).
+    """H_eff of window (i, i+1) from L_i, R_{i+2} and the MPO (Sec. 2.1.2, Sec. 2.3).
 
     Applied to psi: Y = sum_{a,b} (L_a P^{p(a)}) (x) O'_ab (x) R_b, where P is the parity of
     the left ket and O'_ab = O_ab diag((-1)^{p(b) (n(s1) + n(s2))}) carries the sign of

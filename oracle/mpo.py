@@ -1,10 +1,10 @@
 """Exact MPOs of a sum of operator strings (test infrastructure only).
 
-The paper builds MPOs automatically from a symbolic list of operator strings (Sec. 3.2,
+The paper builds MPOs automatically from a symbolic list of operator strings (Sec. 2.3,
 "General MPO construction for Hamiltonians") and, for ab initio Hamiltonians, arranges
 the renormalized operators into normal and complementary sets, switching from the
 normal/complementary (NC) to the complementary/normal (CN) partition at the middle site
-(Sec. 3.2, "Symbolic MPO approach").  Two constructions are written here:
+(Sec. 2.3, "Symbolic MPO approach").  Two constructions are written here:
 
 ``kind="trie"``  the plainest exact MPO: the channels on bond k (between sites k-1 and k)
     are "I" (nothing of the term applied yet), "H" (term complete) and the prefix (the

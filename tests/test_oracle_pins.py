@@ -147,7 +147,7 @@ def test_mpo_dense_conserves_quantum_numbers():
 
 
 def test_ncn_normal_pairs_are_site_ordered_once():
-    # A_ij = -A_ji (Sec. 3.2): a+_i a+_j and a+_j a+_i give ONE normal-operator channel
+    # A_ij = -A_ji (Sec. 2.3): a+_i a+_j and a+_j a+_i give ONE normal-operator channel
     h, eri = ab_initio_integrals(6, seed=5)
     m = mpo.MPO(h, eri)
     for k in range(m.n + 1):
