@@ -47,9 +47,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "window_M1000", "window_M2000"],
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "window_M1000", "window_M2000", "batch64"],
                     help="sweep: Hubbard L=32 M=500 full sweep (default); window_M*: middle "
-                         "window of the n=36 ab initio system, FP64 vs split precision")
+                         "window of the n=36 ab initio system, FP64 vs split precision; "
+                         "batch64: 64 independent problems, grouped vs one-by-one launches")
+    ap.add_argument("--batch", type=int, default=64, help="problems of the batch64 workload")
     return ap.parse_args()
 
 
@@ -307,11 +310,119 @@ def run_window(args):
     ctx.close()
 
 
+def run_batch(args):
+    """64 independent problems (Hubbard L in [12, 40], U in [1, 8]; ab initio n in [10, 24];
+    M in [100, 800]; ``synth.batch_problem``), each from a random MPS centred at its middle
+    window.  Times (a) the H_eff products of all problems one launch each and (b) one
+    grouped launch over all problems (b2_heff_apply_batched), in FP64 and in split precision,
+    and the Davidson solves of all middle windows one by one vs in lockstep
+    (b2_davidson_batched, 30 products at most)."""
+    import numpy as np
+    import torch
+    from paper_2310_03920_gb300 import b2
+    from synth import batch_problem, occupancies, random_mps, sector_sizes
+    ctx = b2.Context(0)
+    t0 = time.perf_counter()
+    probs = []
+    for j in range(args.batch):
+        pr = batch_problem(j)
+        n, N, tsz = pr["n"], pr["n_elec"], pr["two_sz"]
+        c = n // 2 - 1
+        kind = "hubbard" if pr["kind"] == "hubbard" else "ab_initio"
+        bonds = sector_sizes(n, N, tsz, pr["M"], occupancies(n, N, kind))
+        sites = random_mps(bonds, seed=pr["seed"], center=c)
+        mpo = b2.b2_build_mpo(ctx, pr["h"], pr["eri"], 0.0, N, tsz)
+        mps = b2.b2_mps_import(ctx, bonds, sites, N, tsz, center=c)
+        env = b2.b2_env_init(ctx, mpo, mps, center=c)
+        n_elem, _ = b2.b2_psi_layout(ctx, env, c)
+        psi = torch.empty(n_elem, dtype=torch.float64, device="cuda")
+        b2.b2_psi_from_mps(ctx, env, c, psi)
+        probs.append({"mpo": mpo, "mps": mps, "env": env, "site": c, "psi": psi,
+                      "out": torch.empty_like(psi), "kind": pr["kind"], "n": n, "M": pr["M"]})
+    t_setup = time.perf_counter() - t0
+    envs = [p["env"] for p in probs]
+    sites = [p["site"] for p in probs]
+    psis = [p["psi"] for p in probs]
+    outs = [p["out"] for p in probs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        fn()                                   # builds window programs, precombines
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fl = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)), fl
+
+    res = {}
+    for name, prec in (("fp64", b2.B2_FP64), ("bf16x3", b2.B2_BF16X3)):
+        ms_one, fl = timed(lambda: sum(b2.b2_heff_apply(ctx, p["env"], p["site"], p["psi"], p["out"],
+                                                        prec=prec) for p in probs))
+        b2.b2_profile(ctx, True)
+        ms_grp, fl_g = timed(lambda: b2.b2_heff_apply_batched(ctx, envs, sites, psis, outs, prec=prec))
+        prof = b2.b2_profile_read(ctx)
+        b2.b2_profile(ctx, False)
+        res[name] = {"algo_flops": fl, "one_by_one_ms": ms_one, "grouped_ms": ms_grp,
+                     "one_by_one_tflops": fl / (ms_one * 1e-3) / 1e12,
+                     "grouped_tflops": fl_g / (ms_grp * 1e-3) / 1e12,
+                     "speedup": ms_one / ms_grp,
+                     "grouped_launches_per_call": prof["launches"] / (reps + 1)}
+    # Davidson of every middle window: one by one vs lockstep
+    dav = {}
+    for name in ("one_by_one", "lockstep"):
+        ys = [p["psi"].clone() for p in probs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "one_by_one":
+            out = [b2.b2_davidson(ctx, p["env"], p["site"], y, max_iter=30, max_subspace=30,
+                                  conv_tol=1e-10) for p, y in zip(probs, ys)]
+            energies = [o[0] for o in out]
+            nmv = int(sum(o[1] for o in out))
+        else:
+            e, n_mv, _ = b2.b2_davidson_batched(ctx, envs, sites, ys, max_iter=30, max_subspace=30,
+                                                conv_tol=1e-10)
+            energies, nmv = list(e), int(n_mv.sum())
+        torch.cuda.synchronize()
+        dav[name] = {"seconds": time.perf_counter() - t0, "n_matvec": nmv, "energies": energies}
+    same = all(a == b for a, b in zip(dav["one_by_one"]["energies"], dav["lockstep"]["energies"]))
+    for d in dav.values():
+        d.pop("energies")
+    peaks = measured_peaks(torch)
+    g = res["fp64"]
+    line = {"metric": METRIC, "value": g["grouped_tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": reps, "warmup": 1, "ms_per_step": g["grouped_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch%d_middle_windows" % len(probs), "problems": len(probs),
+                       "hubbard": sum(p["kind"] == "hubbard" for p in probs),
+                       "ab_initio": sum(p["kind"] != "hubbard" for p in probs),
+                       "n_range": [min(p["n"] for p in probs), max(p["n"] for p in probs)],
+                       "M_range": [min(p["M"] for p in probs), max(p["M"] for p in probs)],
+                       "l2": "flushed between steps (256 MB write)"},
+            "heff": res, "davidson": dav, "lockstep_energies_identical": same,
+            "fp64_peak_tflops": peaks.get("fp64_tflops_measured"), "setup_s": t_setup}
+    print(json.dumps(line), flush=True)
+    for p in probs:
+        b2.b2_free_env(p["env"])
+        b2.b2_free_mps(p["mps"])
+        b2.b2_free_mpo(p["mpo"])
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch64":
+        run_batch(args)
         return
     if args.workload != "sweep":
         run_window(args)

@@ -3,8 +3,8 @@
  *
  * The method is ab initio two-site DMRG as described in the block2 paper (arXiv
  * 2310.03920): an MPO for the Hamiltonian built from the integrals h_pq and (pq|rs)
- * (Sec. 3.2), renormalized operators (environments) on both sides of a two-site window
- * (Sec. 2.1.2 and Sec. 3.2, "renormalized operator view"), the effective Hamiltonian
+ * (Sec. 2.3), renormalized operators (environments) on both sides of a two-site window
+ * (Sec. 2.1.2 and Sec. 2.3, "renormalized operator view"), the effective Hamiltonian
  * H_eff acting on the two-site wavefunction inside a Davidson eigensolver (Sec. 2.1.3
  * (iv) "standard Davidson solver"; Listing 1: thrds, dav_max_iter), truncation of each
  * bond to M states, and the sweep (Sec. 2.1.2).  Symmetry: particle number and projected
@@ -87,10 +87,10 @@ const char* b2_last_error(b2_ctx ctx);
 /* ----------------------------------------------------------------------------- MPO
  * Ab initio Hamiltonian (Sec. 2.1.1; formula H = E_core + sum_pq h_pq sum_s a+_ps a_qs
  * + 1/2 sum_pqrs (pq|rs) sum_st a+_ps a+_rt a_st a_qs) as an exact MPO built from the
- * operator strings (Sec. 3.2): operators with at most two elementary operators on the
+ * operator strings (Sec. 2.3): operators with at most two elementary operators on the
  * left of a bond are normal operators, the rest are carried as complementary operators,
  * and the partition switches from normal/complementary to complementary/normal after
- * the middle site (Sec. 3.2, "Symbolic MPO approach").
+ * the middle site (Sec. 2.3, "Symbolic MPO approach").
  *   h1   host, n_orb x n_orb row-major, h1[p*n+q] = h_pq (symmetric)
  *   eri  host, n_orb^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs)
  *   integrals with |value| <= cutoff are dropped (0 keeps every nonzero)
@@ -125,7 +125,7 @@ int b2_mps_random(b2_ctx ctx, b2_mpo mpo, int bond_dim, const double* occ, uint6
                   b2_mps* out);
 
 /* --------------------------------------------------------------------- environments
- * Environments (renormalized operators, Sec. 3.2) of every MPO channel: all left
+ * Environments (renormalized operators, Sec. 2.3) of every MPO channel: all left
  * environments L_0..L_center built from the left-orthonormal sites and all right
  * environments R_{center+2}..R_n from the right-orthonormal sites.  The env keeps
  * references to mpo and mps, which must outlive it. */
@@ -210,6 +210,35 @@ typedef struct {
 int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts* opts,
              b2_sweep_result* per_sweep);
 
+/* ------------------------------------------------------- many independent problems
+ * Batched execution of independent problems on one context (one GPU, one stream): the
+ * paper runs one large problem with MPI strategies (Sec. 2.2); for many small ones, which
+ * alone leave most of a GB300 idle, these calls advance all problems in lockstep and issue
+ * ONE grouped launch of the H_eff contraction over every problem's window per Davidson
+ * iteration.  Per problem, the kernels, their arguments and their order are those of the
+ * single-problem calls, so each result equals that of b2_heff_apply / b2_davidson /
+ * b2_sweep on the same problem.  All envs must belong to ctx and be distinct (a window's
+ * work space is per env); the psi / out buffers of different problems must not overlap.
+ *
+ * b2_heff_apply_batched: out_i = H_eff(envs[i], sites[i]) psi_i for i < n (device
+ *   vectors in each window's layout; prec B2_FP64 or B2_BF16X3); *algo_flops (may be
+ *   NULL) = sum of the problems' algorithmic flops.  No e_shift.
+ * b2_davidson_batched: b2_davidson on every (envs[i], sites[i], psis[i]) with the same
+ *   options; energies / n_matvec / resid2 (host, n entries each, may be NULL).
+ * b2_sweep_batched: b2_sweep (same options) on every env's MPO and MPS; window step t of a
+ *   sweep is window t of the forward half or window 2(n-1)-1-t of the backward half of
+ *   each problem (problems with fewer sites finish earlier).  results: host,
+ *   n * n_sweeps entries, problem-major; seconds, t_davidson and t_split are those of the
+ *   whole batch. */
+int b2_heff_apply_batched(b2_ctx ctx, int n, const b2_env* envs, const int* sites,
+                          const double* const* psis, double* const* outs, b2_prec prec,
+                          double* algo_flops);
+int b2_davidson_batched(b2_ctx ctx, int n, const b2_env* envs, const int* sites,
+                        double* const* psis, const b2_dav_opts* opts, double* energies,
+                        int* n_matvec, double* resid2);
+int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts* opts,
+                     b2_sweep_result* results);
+
 /* ------------------------------------------------------------------ batched eigensolver
  * Eigen-decomposition of n_mat real symmetric matrices by cyclic Jacobi rotations in
  * FP64, one thread block per matrix: the density-matrix step of the truncation.
@@ -240,6 +269,25 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
  *   stream-ordered and returns without waiting for the result. */
 int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, const double* a,
                            double* evals, double* evecs);
+
+/* ----------------------------------------------------------------- integral gradient
+ * Gradient of the energy E = <psi|H|psi> / <psi|psi> of the MPS with respect to the
+ * integrals of the Hamiltonian of Sec. 2.1.1, at fixed psi: the spin-traced one- and
+ * two-particle density matrices of Sec. 2.5.1,
+ *   dE/dh_pq      = gamma_pq      = sum_s    <a+_ps a_qs>
+ *   dE/d(pq|rs)   = Gamma_pqrs / 2,  Gamma_pqrs = sum_st <a+_ps a+_rt a_st a_qs>,
+ * every array element taken as an independent variable (E is linear in each; at a
+ * converged ground state this is also the derivative of the ground-state energy).  The
+ * mpo only names the system (n, electrons, 2Sz must match the mps): the gradient covers
+ * every integral, also those that are zero in mpo.  The computation is the backward pass
+ * of the one-site energy <psi| L (x) W_k (x) R |psi> with respect to each MPO entry at
+ * each site k (the adjoint of the effective Hamiltonian), chained with the MPO builder's
+ * coefficient Jacobian; it runs on a private copy of the MPS, whose centre must be at
+ * site 0 (as b2_sweep leaves it).
+ *   h1_grad   host, n*n FP64, row-major: gamma
+ *   eri_grad  host, n^4 FP64, chemist order (pq|rs): Gamma / 2
+ * Errors: B2_EINVAL (mismatched system, centre not 0, zero norm), B2_ECUDA. */
+int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri_grad);
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every

@@ -70,6 +70,10 @@ _sig = {
     "b2_sweep": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepResult)]),
     "b2_eigh_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "b2_eigh_batched_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "b2_rdm_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "b2_heff_apply_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_d)]),
+    "b2_davidson_batched": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(DavOpts), _vp, _vp, _vp]),
+    "b2_sweep_batched": (_i, [_vp, _i, _vp, ctypes.POINTER(SweepOpts), _vp]),
     "b2_profile": (_i, [_vp, _i]),
     "b2_profile_read": (_i, [_vp, ctypes.POINTER(ProfileData)]),
     "b2_free_mpo": (None, [_vp]),
@@ -277,6 +281,57 @@ def b2_eigh_batched_static(ctx, dims, a, evals, evecs):
     d = np.ascontiguousarray(dims, dtype=np.int32)
     _check(ctx.h, lib.b2_eigh_batched_static(ctx.h, len(d), d.ctypes.data, _ptr(a), _ptr(evals),
                                              _ptr(evecs)))
+
+
+def _handles(hs):
+    return (_vp * len(hs))(*[h.value if isinstance(h, _vp) else h for h in hs])
+
+
+def _dev_ptrs(ts):
+    return (_vp * len(ts))(*[_ptr(t).value for t in ts])
+
+
+def b2_heff_apply_batched(ctx, envs, sites, psis, outs, prec=B2_FP64):
+    """One grouped launch of the H_eff products of several problems' windows."""
+    n = len(envs)
+    st = (_i * n)(*sites)
+    fl = _d()
+    _check(ctx.h, lib.b2_heff_apply_batched(ctx.h, n, _handles(envs), st, _dev_ptrs(psis),
+                                            _dev_ptrs(outs), prec, ctypes.byref(fl)))
+    return fl.value
+
+
+def b2_davidson_batched(ctx, envs, sites, psis, max_iter=30, max_subspace=30, conv_tol=1e-10,
+                        prec=B2_FP64, refine_max=0):
+    n = len(envs)
+    o = DavOpts(max_iter, max_subspace, conv_tol, prec, refine_max)
+    e = np.zeros(n)
+    nmv = np.zeros(n, dtype=np.int32)
+    r2 = np.zeros(n)
+    _check(ctx.h, lib.b2_davidson_batched(ctx.h, n, _handles(envs), (_i * n)(*sites),
+                                          _dev_ptrs(psis), ctypes.byref(o), e.ctypes.data,
+                                          nmv.ctypes.data, r2.ctypes.data))
+    return e, nmv, r2
+
+
+def b2_sweep_batched(ctx, envs, bond_dims, conv_tol=1e-10, dav_max_iter=30, max_subspace=30,
+                     prec=B2_FP64, trunc_cutoff=1e-14):
+    n = len(envs)
+    bd = (_i * len(bond_dims))(*bond_dims)
+    o = SweepOpts(len(bond_dims), bd, conv_tol, dav_max_iter, max_subspace, prec, trunc_cutoff)
+    res = (SweepResult * (n * len(bond_dims)))()
+    _check(ctx.h, lib.b2_sweep_batched(ctx.h, n, _handles(envs), ctypes.byref(o), res))
+    k = len(bond_dims)
+    return [[{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res[p * k:(p + 1) * k]]
+            for p in range(n)]
+
+
+def b2_rdm_grad(ctx, mpo, mps, n):
+    """(gamma [n, n], Gamma / 2 [n, n, n, n]) as numpy FP64: dE/dh and dE/d(pq|rs)."""
+    g1 = np.zeros((n, n), dtype=np.float64)
+    g2 = np.zeros((n, n, n, n), dtype=np.float64)
+    _check(ctx.h, lib.b2_rdm_grad(ctx.h, mpo, mps, g1.ctypes.data, g2.ctypes.data))
+    return g1, g2
 
 
 def b2_profile(ctx, enable=True):

@@ -274,6 +274,15 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     }
     for (int t = 0; t < dims[j]; ++t) sec_of.push_back(j);
   }
+  if (std::getenv("B2_TRACE_TIME")) {
+    std::vector<int> sd(dims.begin(), dims.end());
+    std::sort(sd.rbegin(), sd.rend());
+    double cubes = 0;
+    for (int d : sd) cubes += double(d) * d * d;
+    std::fprintf(stderr, "trace rho sectors %d dims %d %d %d %d sum_m3 %.3g\n", ns,
+                 sd.size() > 0 ? sd[0] : 0, sd.size() > 1 ? sd[1] : 0, sd.size() > 2 ? sd[2] : 0,
+                 sd.size() > 3 ? sd[3] : 0, cubes);
+  }
   B2_REQUIRE(max_dim <= 1024, B2_EUNSUPPORTED, "density-matrix sector larger than 1024");
   B2_REQUIRE(tot_e <= b2k::kSelectMax, B2_EUNSUPPORTED, "too many density-matrix eigenvalues");
   DevBuf d_dims, d_offs, d_eoffs, d_woffs, d_sec, work, d_kept(c, sizeof(int) * ns + 16),

@@ -19,5 +19,16 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
 void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
                  double* flops, bool make_guess);
 void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res);
+// Many independent problems in lockstep, one grouped H_eff launch per Davidson iteration
+// (batch.cpp); per problem identical to davidson / sweep.
+std::vector<DavidsonResult> davidson_batched(Ctx* c, const std::vector<b2_env_s*>& envs,
+                                             const std::vector<int>& sites,
+                                             const std::vector<double*>& psis,
+                                             const b2_dav_opts& o);
+void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_opts& o,
+                   b2_sweep_result* res);
+// Integral gradient (spin-traced 1- and 2-particle density matrices) of the MPS energy;
+// host outputs, see b2_rdm_grad.
+void rdm_grad(Ctx* c, b2_mpo_s* mpo, b2_mps_s* mps, double* h1_grad, double* eri_grad);
 
 }  // namespace b2

@@ -314,6 +314,68 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
   });
 }
 
+int b2_heff_apply_batched(b2_ctx ctx, int n, const b2_env* envs, const int* sites,
+                          const double* const* psis, double* const* outs, b2_prec prec,
+                          double* algo_flops) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(n >= 0, B2_EINVAL, "n < 0");
+    if (n == 0) return;
+    B2_REQUIRE(envs && sites && psis && outs, B2_EINVAL, "null argument");
+    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3, B2_EUNSUPPORTED,
+               "precision not implemented in this build");
+    for (int i = 0; i < n; ++i) check_env(ctx, envs[i]);
+    ensure_device(ctx);
+    b2::heff_apply_batched(&ctx->c, n, envs, sites, psis, outs, prec, algo_flops);
+  });
+}
+
+int b2_davidson_batched(b2_ctx ctx, int n, const b2_env* envs, const int* sites,
+                        double* const* psis, const b2_dav_opts* opts, double* energies,
+                        int* n_matvec, double* resid2) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(n >= 0, B2_EINVAL, "n < 0");
+    if (n == 0) return;
+    B2_REQUIRE(envs && sites && psis && opts, B2_EINVAL, "null argument");
+    for (int i = 0; i < n; ++i) {
+      check_env(ctx, envs[i]);
+      B2_REQUIRE(psis[i] != nullptr, B2_EINVAL, "null psi");
+    }
+    ensure_device(ctx);
+    std::vector<b2_env_s*> e(envs, envs + n);
+    std::vector<int> s(sites, sites + n);
+    std::vector<double*> p(psis, psis + n);
+    std::vector<b2::DavidsonResult> r = b2::davidson_batched(&ctx->c, e, s, p, *opts);
+    for (int i = 0; i < n; ++i) {
+      if (energies) energies[i] = r[i].energy;
+      if (n_matvec) n_matvec[i] = r[i].n_matvec;
+      if (resid2) resid2[i] = r[i].resid2;
+    }
+  });
+}
+
+int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts* opts,
+                     b2_sweep_result* results) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(n >= 0, B2_EINVAL, "n < 0");
+    if (n == 0) return;
+    B2_REQUIRE(envs && opts && opts->bond_dims && opts->n_sweeps >= 0, B2_EINVAL,
+               "bad batched sweep arguments");
+    for (int i = 0; i < n; ++i) check_env(ctx, envs[i]);
+    ensure_device(ctx);
+    std::vector<b2_env_s*> e(envs, envs + n);
+    b2::sweep_batched(&ctx->c, e, *opts, results);
+  });
+}
+
+int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri_grad) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(ctx && mpo && mps && h1_grad && eri_grad, B2_EINVAL, "null argument");
+    B2_REQUIRE(mps->ctx == &ctx->c, B2_EINVAL, "mps belongs to another context");
+    ensure_device(ctx);
+    b2::rdm_grad(&ctx->c, mpo, mps, h1_grad, eri_grad);
+  });
+}
+
 int b2_profile(b2_ctx ctx, int enable) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx, B2_EINVAL, "null context");

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <cstring>
 #include <memory>
@@ -170,6 +171,22 @@ struct b2_mpo_s {
     double m[16];   // local operator, row = output state
   };
   std::vector<std::vector<Entry>> W;                 // per site
+  // Coefficient Jacobian (for energy gradients).  Every distinct site-ordered operator
+  // string s has one MPO entry where its coefficient c_s enters, W_site[w, w2] += c_s * op;
+  // every spin-orbital term of the Hamiltonian adds sign * (h_pq or eri_pqrs / 2) to one
+  // string's coefficient.
+  struct StringEntry {
+    int site, w, w2, op;   // op: index into ops, -1 = identity; site -1: coefficient zero
+  };
+  std::vector<StringEntry> str_entry;
+  struct TermRec {
+    int32_t str;
+    int32_t integral;      // p*n+q (h) or ((p*n+q)*n+r)*n+s (eri)
+    int8_t kind;           // 0: h, 1: eri (coefficient eri / 2)
+    int8_t sign;
+  };
+  std::vector<TermRec> terms;
+  std::vector<std::array<double, 16>> ops;           // local operator table
 };
 
 struct b2_mps_s {

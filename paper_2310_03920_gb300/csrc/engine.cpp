@@ -1,6 +1,6 @@
 // Environments (renormalized operators), the two-site effective Hamiltonian and its
 // diagonal, expressed as block-GEMM programs for the FP64 kernels (block2 paper: Sec.
-// 2.1.2 for the two-site wavefunction, Sec. 3.2 for the MPO / renormalized-operator
+// 2.1.2 for the two-site wavefunction, Sec. 2.3 for the MPO / renormalized-operator
 // view).
 //
 // Fermion signs.  Every MPO channel w carries the parity p(w) of its left part.  On a ket
@@ -49,34 +49,107 @@ void GemmProgram::add_term(int out, const GemmTerm& t) {
     flops += 2.0 * o.M * t.K1 * t.K2 + 2.0 * o.M * double(t.K2) * o.N;
 }
 
+// Work distribution of the FP64 kernel.  The cost of a 32 x 32 tile is the flops its CTA
+// performs (operands padded to 32): 2*32*32*K1 for a 2-operand term, 2*32*K1*K2 +
+// 2*32*32*K2 for a 3-operand one.  Tiles are split into term ranges of about equal cost
+// when the program would otherwise leave SMs idle: the target cost of an item is the total
+// over kSplitItems items, at least kMinItemFlops.
+namespace {
+constexpr double kSplitItems = 4.0 * 152;
+constexpr double kMinItemFlops = 1.0e5;
+inline int pad32(int x) { return (x + 31) & ~31; }
+double term_tile_flops(const GemmTerm& t) {
+  if (t.flags & kTwoOp) return 2.0 * 32 * 32 * pad32(t.K1);
+  return 2.0 * 32 * pad32(t.K1) * pad32(t.K2) + 2.0 * 32 * 32 * pad32(t.K2);
+}
+}  // namespace
+
 void GemmProgram::finalize(Ctx* c, bool with_tc) {
   terms.clear();
-  tiles.clear();
+  tasks.clear();
+  reds.clear();
   tiles_tc.clear();
+  std::vector<double> tcost;   // per term
+  double total = 0;
   for (size_t i = 0; i < outs.size(); ++i) {
     auto& o = outs[i];
     o.t0 = int(terms.size());
     terms.insert(terms.end(), by_out[i].begin(), by_out[i].end());
     o.t1 = int(terms.size());
+    double per_tile = 0;
+    for (const auto& t : by_out[i]) {
+      tcost.push_back(term_tile_flops(t));
+      per_tile += tcost.back();
+    }
+    if (o.M > 0 && o.N > 0 && !(o.accumulate && o.t0 == o.t1))
+      total += per_tile * double((o.M + 31) / 32) * double((o.N + 31) / 32);
+  }
+  const double target = std::max(total / kSplitItems, kMinItemFlops);
+  int slots = 0;
+  for (size_t i = 0; i < outs.size(); ++i) {
+    const auto& o = outs[i];
     if (o.M == 0 || o.N == 0) continue;
     if (o.accumulate && o.t0 == o.t1) continue;
+    // term ranges of about equal cost (the same for every tile of this output)
+    std::vector<std::pair<int, int>> ranges;
+    double per_tile = 0;
+    for (int t = o.t0; t < o.t1; ++t) per_tile += tcost[t];
+    const int n_split = std::max(1, std::min(o.t1 - o.t0, int(std::ceil(per_tile / target))));
+    if (n_split == 1) {
+      ranges.push_back({o.t0, o.t1});
+    } else {
+      const double chunk = per_tile / n_split;
+      double accum = 0;
+      int start = o.t0;
+      for (int t = o.t0; t < o.t1; ++t) {
+        accum += tcost[t];
+        if (accum >= chunk * double(ranges.size() + 1) && int(ranges.size()) + 1 < n_split) {
+          ranges.push_back({start, t + 1});
+          start = t + 1;
+        }
+      }
+      ranges.push_back({start, o.t1});
+    }
     for (int r = 0; r < o.M; r += b2k::kTile)
-      for (int cc = 0; cc < o.N; cc += b2k::kTile) tiles.push_back({int(i), r, cc});
+      for (int cc = 0; cc < o.N; cc += b2k::kTile) {
+        if (ranges.size() == 1) {
+          tasks.push_back({int(i), r, cc, ranges[0].first, ranges[0].second, -1});
+        } else {
+          reds.push_back({int(i), r, cc, slots, int(ranges.size())});
+          for (const auto& rg : ranges) tasks.push_back({int(i), r, cc, rg.first, rg.second, slots++});
+        }
+      }
     if (with_tc)
       for (int r = 0; r < o.M; r += b2k::kTcTile)
         for (int cc = 0; cc < o.N; cc += b2k::kTcTile) tiles_tc.push_back({int(i), r, cc});
   }
+  // most expensive items first (they are dispatched first)
+  std::vector<double> cost(tasks.size());
+  for (size_t k = 0; k < tasks.size(); ++k) {
+    double x = 0;
+    for (int t = tasks[k].t0; t < tasks[k].t1; ++t) x += tcost[t];
+    cost[k] = x;
+  }
+  std::vector<int> order(tasks.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = int(k);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<b2k::GemmTask> sorted(tasks.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = tasks[order[k]];
+  tasks.swap(sorted);
   B2_REQUIRE(terms.size() < (1u << 31), B2_EUNSUPPORTED, "too many contraction terms");
   by_out.clear();
   by_out.shrink_to_fit();
   upload(c, d_terms, terms);
   upload(c, d_outs, outs);
-  upload(c, d_tiles, tiles);
+  upload(c, d_tasks, tasks);
+  upload(c, d_reds, reds);
+  if (slots > 0) d_partial.reset(c, sizeof(double) * size_t(slots) * b2k::kTile * b2k::kTile);
   if (with_tc) upload(c, d_tiles_tc, tiles_tc);
 }
 
 void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
-  b2k::launch_gemm(d_tiles.as<b2k::GemmTile>(), int(tiles.size()), d_outs.as<b2k::GemmOut>(),
+  b2k::launch_gemm(d_tasks.as<b2k::GemmTask>(), int(tasks.size()), d_reds.as<b2k::GemmReduce>(),
+                   int(reds.size()), d_partial.as<double>(), d_outs.as<b2k::GemmOut>(),
                    d_terms.as<GemmTerm>(), bt, c->stream);
   B2_CUDA(cudaGetLastError());
 }
@@ -615,6 +688,70 @@ void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double 
   }
   if (e_shift != 0.0) b2k::launch_axpby(out, psi, wp.psi.size, 1.0, -e_shift, c->stream);
   if (flops) *flops = wp.heff.flops;
+}
+
+void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
+                        const double* const* psis, double* const* outs, b2_prec prec,
+                        double* flops) {
+  std::vector<b2k::GemmGroup> groups;
+  std::vector<b2k::GemmGroupTc> groups_tc;
+  int items = 0, reds = 0, tiles = 0;
+  double fl = 0;
+  for (int i = 0; i < n; ++i) {
+    b2_env_s* env = envs[i];
+    B2_REQUIRE(env->ctx == c, B2_EINVAL, "batched H_eff: env of another context");
+    for (int j = 0; j < i; ++j)
+      B2_REQUIRE(envs[j] != env, B2_EINVAL, "batched H_eff: the same env twice");
+    const int site = sites[i];
+    WindowProgram& wp = window_program(env, site);
+    B2_REQUIRE(psis[i] != outs[i], B2_EINVAL, "batched H_eff: out aliases psi");
+    BufTable bt{};
+    bt.p[0] = const_cast<double*>(psis[i]);
+    bt.p[1] = outs[i];
+    bt.p[2] = env->L[site].data.as<double>();
+    bt.p[3] = env->R[site + 2].data.as<double>();
+    bt.p[4] = wp.comb_buf.as<double>();
+    if (!wp.comb_done) {
+      if (wp.comb_buf.ptr) wp.comb.launch(c, bt);
+      wp.comb_done = true;
+    }
+    if (prec == B2_FP64) {
+      groups.push_back({wp.heff.d_tasks.as<b2k::GemmTask>(), wp.heff.d_reds.as<b2k::GemmReduce>(),
+                        wp.heff.d_outs.as<b2k::GemmOut>(), wp.heff.d_terms.as<GemmTerm>(),
+                        wp.heff.d_partial.as<double>(), bt, items, reds});
+      items += int(wp.heff.tasks.size());
+      reds += int(wp.heff.reds.size());
+    } else {
+      groups_tc.push_back({wp.heff.d_tiles_tc.as<b2k::GemmTile>(), wp.heff.d_outs.as<b2k::GemmOut>(),
+                           wp.heff.d_terms.as<GemmTerm>(), bt, tiles});
+      tiles += int(wp.heff.tiles_tc.size());
+    }
+    fl += wp.heff.flops;
+  }
+  DevBuf d_groups;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    B2_CUDA(cudaEventCreate(&e0));
+    B2_CUDA(cudaEventCreate(&e1));
+  }
+  if (prec == B2_FP64) {
+    upload(c, d_groups, groups);
+    if (e0) B2_CUDA(cudaEventRecord(e0, c->stream));
+    b2k::launch_gemm_grouped(d_groups.as<b2k::GemmGroup>(), int(groups.size()), items, reds,
+                             c->stream);
+  } else {
+    upload(c, d_groups, groups_tc);
+    if (e0) B2_CUDA(cudaEventRecord(e0, c->stream));
+    b2k::launch_gemm_tc_grouped(d_groups.as<b2k::GemmGroupTc>(), int(groups_tc.size()), tiles,
+                                c->status(), c->stream);
+  }
+  B2_CUDA(cudaGetLastError());
+  if (e0) {
+    B2_CUDA(cudaEventRecord(e1, c->stream));
+    c->prof_events.push_back({e0, e1});
+    c->prof_flops += fl;
+  }
+  if (flops) *flops = fl;
 }
 
 void heff_diag(b2_env_s* env, int site, double* diag) {

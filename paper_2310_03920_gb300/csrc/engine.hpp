@@ -13,15 +13,17 @@ struct GemmProgram {
   std::vector<std::vector<b2k::GemmTerm>> by_out;
   std::vector<b2k::GemmOut> outs;
   std::vector<b2k::GemmTerm> terms;
-  std::vector<b2k::GemmTile> tiles, tiles_tc;   // 32x32 FP64 tiles, 128x128 tensor-core tiles
-  DevBuf d_terms, d_outs, d_tiles, d_tiles_tc;
+  std::vector<b2k::GemmTask> tasks;              // FP64 work items (32x32 tiles, term ranges)
+  std::vector<b2k::GemmReduce> reds;             // fixed-order sums of split tiles
+  std::vector<b2k::GemmTile> tiles_tc;           // 128x128 tensor-core tiles
+  DevBuf d_terms, d_outs, d_tasks, d_reds, d_partial, d_tiles_tc;
   double flops = 0;
   int add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate);
   void add_term(int out, const b2k::GemmTerm& t);
   void finalize(Ctx* c, bool with_tc = false);
   void launch(Ctx* c, const b2k::BufTable& bt) const;
   void launch_tc(Ctx* c, const b2k::BufTable& bt) const;
-  bool empty() const { return tiles.empty(); }
+  bool empty() const { return tasks.empty(); }
 };
 
 struct CombProgram {
@@ -95,4 +97,10 @@ void env_update_right(b2_env_s* env, int site);
 void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
                 double* flops, b2_prec prec = B2_FP64);
 void heff_diag(b2_env_s* env, int site, double* diag);
+// H_eff products of the windows (envs[i], sites[i]) of independent problems on context c
+// in one grouped launch (FP64: k_gemm_grouped + k_gemm_reduce_grouped; split precision:
+// k_gemm_tc_grouped).  Each work item runs exactly the code of the single-problem launch.
+void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
+                        const double* const* psis, double* const* outs, b2_prec prec,
+                        double* flops);
 }  // namespace b2

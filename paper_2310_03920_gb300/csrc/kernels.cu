@@ -6,8 +6,13 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <mutex>
+
+#include <cooperative_groups.h>
 
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace b2k {
 
@@ -16,10 +21,12 @@ long long launch_count() { return g_launches.load(); }
 void count_launches(int n) { g_launches += n; }
 
 // ============================================================ block GEMM (FP64)
-// One CTA of 128 threads owns a 32 x 32 tile of one output block and adds every term of
-// that block in order (no atomics, deterministic).  A 3-operand term is evaluated as
-// sum over 32-wide chunks c of K2 of (op(P) X[:, c]) op(Q)[c, :], keeping the
-// intermediate chunk in shared memory.
+// One CTA of 128 threads takes one work item: a 32 x 32 tile of one output block and a
+// range of that block's terms, added in order.  Items that own their tile write it; tiles
+// whose terms are split over several items (so that small programs still fill the GPU)
+// get per-item partial tiles that k_gemm_reduce adds in a fixed order: no atomics,
+// deterministic.  A 3-operand term is evaluated as sum over 32-wide chunks c of K2 of
+// (op(P) X[:, c]) op(Q)[c, :], keeping the intermediate chunk in shared memory.
 __device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* M, int ld,
                                           int rows, int cols, int r0, int c0, bool trans,
                                           int tid) {
@@ -39,17 +46,16 @@ __device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* 
   }
 }
 
-__global__ void __launch_bounds__(128) k_gemm(const GemmTile* __restrict__ tiles,
-                                              const GemmOut* __restrict__ outs,
-                                              const GemmTerm* __restrict__ terms, BufTable bt) {
+__device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* __restrict__ outs,
+                                          const GemmTerm* __restrict__ terms, const BufTable& bt,
+                                          double* __restrict__ partial) {
   __shared__ double Ps[kTile][kTile + 1], Xs[kTile][kTile + 1];
   __shared__ double Ts[kTile][kTile + 1], Qs[kTile][kTile + 1];
-  const GemmTile tile = tiles[blockIdx.x];
   const GemmOut o = outs[tile.out];
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const int r0 = tile.r0, c0 = tile.c0;
   double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  for (int t = o.t0; t < o.t1; ++t) {
+  for (int t = tile.t0; t < tile.t1; ++t) {
     const GemmTerm g = terms[t];
     const double* P = bt.p[g.bufP] + g.offP;
     const double* X = bt.p[g.bufX] + g.offX;
@@ -117,6 +123,14 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmTile* __restrict__ tiles
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = fma(g.alpha, tacc[a][b], acc[a][b]);
   }
+  if (tile.slot >= 0) {
+    double* pt = partial + int64_t(tile.slot) * (kTile * kTile);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) pt[(2 * ty + a) * kTile + 4 * tx + b] = acc[a][b];
+    return;
+  }
   double* out = bt.p[o.buf] + o.off;
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
@@ -132,10 +146,80 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmTile* __restrict__ tiles
   }
 }
 
-void launch_gemm(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                 const BufTable& bt, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  k_gemm<<<n_tiles, 128, 0, s>>>(tiles, outs, terms, bt);
+__global__ void __launch_bounds__(128) k_gemm(const GemmTask* __restrict__ tasks,
+                                              const GemmOut* __restrict__ outs,
+                                              const GemmTerm* __restrict__ terms, BufTable bt,
+                                              double* __restrict__ partial) {
+  gemm_item(tasks[blockIdx.x], outs, terms, bt, partial);
+}
+
+// Grouped launch over the programs of several independent problems: CTA b takes item
+// b - item0 of the group g with item0(g) <= b < item0(g + 1).
+__device__ __forceinline__ int find_group(const GemmGroup* __restrict__ groups, int n_groups,
+                                          int b, bool reds) {
+  int lo = 0, hi = n_groups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int start = reds ? groups[mid].red0 : groups[mid].item0;
+    if (start <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) k_gemm_grouped(const GemmGroup* __restrict__ groups,
+                                                      int n_groups) {
+  const int g = find_group(groups, n_groups, blockIdx.x, false);
+  const GemmGroup& G = groups[g];
+  const BufTable bt = G.bt;
+  gemm_item(G.tasks[blockIdx.x - G.item0], G.outs, G.terms, bt, G.partial);
+}
+
+__device__ __forceinline__ void reduce_item(const GemmReduce& rd, const GemmOut* __restrict__ outs,
+                                            const BufTable& bt, const double* __restrict__ partial) {
+  const GemmOut o = outs[rd.out];
+  double* out = bt.p[o.buf] + o.off;
+  for (int e = threadIdx.x; e < kTile * kTile; e += 128) {
+    const int r = rd.r0 + e / kTile, c = rd.c0 + e % kTile;
+    if (r >= o.M || c >= o.N) continue;
+    double v = 0.0;
+    for (int k = 0; k < rd.n; ++k) v += partial[int64_t(rd.slot0 + k) * (kTile * kTile) + e];
+    double* p = out + int64_t(r) * o.ld + c;
+    *p = o.accumulate ? *p + v : v;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_reduce(const GemmReduce* __restrict__ reds,
+                                                     const GemmOut* __restrict__ outs, BufTable bt,
+                                                     const double* __restrict__ partial) {
+  reduce_item(reds[blockIdx.x], outs, bt, partial);
+}
+
+__global__ void __launch_bounds__(128) k_gemm_reduce_grouped(const GemmGroup* __restrict__ groups,
+                                                             int n_groups) {
+  const int g = find_group(groups, n_groups, blockIdx.x, true);
+  const GemmGroup& G = groups[g];
+  const BufTable bt = G.bt;
+  reduce_item(G.reds[blockIdx.x - G.red0], G.outs, bt, G.partial);
+}
+
+void launch_gemm_grouped(const GemmGroup* groups, int n_groups, int n_items, int n_reds,
+                         cudaStream_t s) {
+  if (n_groups <= 0 || n_items <= 0) return;
+  k_gemm_grouped<<<n_items, 128, 0, s>>>(groups, n_groups);
+  g_launches += 1;
+  if (n_reds <= 0) return;
+  k_gemm_reduce_grouped<<<n_reds, 128, 0, s>>>(groups, n_groups);
+  g_launches += 1;
+}
+
+void launch_gemm(const GemmTask* tasks, int n_tasks, const GemmReduce* reds, int n_reds,
+                 double* partial, const GemmOut* outs, const GemmTerm* terms, const BufTable& bt,
+                 cudaStream_t s) {
+  if (n_tasks <= 0) return;
+  k_gemm<<<n_tasks, 128, 0, s>>>(tasks, outs, terms, bt, partial);
+  g_launches += 1;
+  if (n_reds <= 0) return;
+  k_gemm_reduce<<<n_reds, 128, 0, s>>>(reds, outs, bt, partial);
   g_launches += 1;
 }
 
@@ -236,17 +320,30 @@ __host__ __device__ inline size_t jacobi_smem_bytes(int m) {
   return mat + aux;
 }
 
+// row-major rank e of the upper triangle (i <= j < half) -> (i, j); the float estimate
+// is corrected with exact integer arithmetic
+__device__ __forceinline__ void unrank_upper(int e, int half, int& i, int& j) {
+  const float h = 2.0f * half + 1.0f;
+  i = int((h - sqrtf(fmaxf(h * h - 8.0f * float(e), 0.0f))) * 0.5f);
+  i = max(0, min(i, half - 1));
+  while (i > 0 && i * half - i * (i - 1) / 2 > e) --i;
+  while ((i + 1) * half - (i + 1) * i / 2 <= e) ++i;
+  j = i + (e - (i * half - i * (i - 1) / 2));
+}
+
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict__ dims,
                                                            const int64_t* __restrict__ offs,
                                                            const int64_t* __restrict__ eoffs,
                                                            const double* __restrict__ a,
                                                            double* evals, double* evecs,
                                                            double* work,
-                                                           const int64_t* __restrict__ woffs) {
+                                                           const int64_t* __restrict__ woffs,
+                                                           int max_m) {
   extern __shared__ double smem[];
   __shared__ int nrot;
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int m = dims[b];
+  if (m > max_m) return;   // left to k_jacobi_cluster
   const int mp = m + (m & 1), half = mp / 2;
   double *A, *Vt;
   double* next = smem;
@@ -310,12 +407,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
       // A <- J^T A J, one 2x2 block (pair i rows, pair j columns) per work item, i <= j
       for (int e = tid; e < nblk; e += nt) {
         // unrank e -> (i, j), 0 <= i <= j < half, row-major over the upper triangle
-        int i = int((2.0 * half + 1.0 - sqrt((2.0 * half + 1.0) * (2.0 * half + 1.0) - 8.0 * e)) * 0.5);
-        while (i > 0 && i * half - i * (i - 1) / 2 > e) --i;
-        while ((i + 1) * half - (i + 1) * i / 2 <= e) ++i;
-        const int j = i + (e - (i * half - i * (i - 1) / 2));
-        const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
+        int i, j;
+        unrank_upper(e, half, i, j);
         const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (si == 0.0 && sj == 0.0) continue;   // identity on this block: nothing changes
+        const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
         if (q >= 0 && u >= 0) {
           double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
           // rows: [c -s; s c] applied on (p, q); columns likewise on (r, u)
@@ -341,14 +437,15 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
         }
       }
       // V <- V J: rows p, q of V^T
-      for (int e = tid; e < half * m; e += nt) {
-        int i = e / m, k = e % m;
-        int p = pi_[i], q = qi_[i];
-        double c = cs[i], s = sn[i];
+      for (int i = tid >> 5; i < half; i += nt >> 5) {
+        const int p = pi_[i], q = qi_[i];
+        const double c = cs[i], s = sn[i];
         if (q < 0 || s == 0.0) continue;
-        double vp = Vt[p * m + k], vq = Vt[q * m + k];
-        Vt[p * m + k] = c * vp - s * vq;
-        Vt[q * m + k] = s * vp + c * vq;
+        for (int k = tid & 31; k < m; k += 32) {
+          double vp = Vt[p * m + k], vq = Vt[q * m + k];
+          Vt[p * m + k] = c * vp - s * vq;
+          Vt[q * m + k] = s * vp + c * vq;
+        }
       }
       for (int i = tid; i < mp; i += nt)   // round-robin: keep perm[0], rotate the rest
         perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
@@ -374,19 +471,207 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
   }
 }
 
+// The same rotation sequence for one large matrix (dim > kJacobiSmemAV) spread over a
+// cluster of kJacobiCluster CTAs: GB300's FP64 rate per SM is low, so one SM per large
+// matrix bounds the whole truncation.  A and V^T stay in the global work space (L2
+// resident); every round, the cluster's threads compute the rotations of disjoint pairs
+// into rank 0's shared memory, synchronise, copy them to their own shared memory and
+// update disjoint 2 x 2 blocks of A and rows of V^T, then synchronise again.  Each element
+// sees the same operations in the same order as in k_jacobi, so the results are identical.
+// One cluster per matrix: the grid is n_mat clusters, clusters of small matrices return at
+// once (uniformly, before any cluster barrier).
+__device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) {
+  __threadfence();
+  cl.sync();
+}
+
+__host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
+  const int mp = m + (m & 1), half = mp / 2;
+  return size_t(half) * (2 * sizeof(double) + 2 * sizeof(int)) + size_t(mp) * 2 * sizeof(int) +
+         4 * sizeof(int);
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
+    const int* __restrict__ dims, const int64_t* __restrict__ offs,
+    const int64_t* __restrict__ eoffs, const double* __restrict__ a, double* evals,
+    double* evecs, double* work, const int64_t* __restrict__ woffs) {
+  extern __shared__ double smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = int(cl.num_blocks());
+  const int crank = int(cl.block_rank());
+  const int b = blockIdx.x / C;
+  const int m = dims[b];
+  if (m <= kJacobiSmemAV) return;   // whole cluster: handled by k_jacobi
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int gt = crank * nt + tid, gn = C * nt;
+  const int mp = m + (m & 1), half = mp / 2;
+  double* A = work + woffs[b];
+  double* Vt = A + size_t(m) * m;
+  double* cs = smem;
+  double* sn = cs + half;
+  int* pi_ = reinterpret_cast<int*>(sn + half);
+  int* qi_ = pi_ + half;
+  int* perm = qi_ + half;
+  int* perm2 = perm + mp;
+  int* cnt = perm2 + mp;
+  // rank 0's arrays are the exchange area
+  double* cs0 = cl.map_shared_rank(cs, 0);
+  double* sn0 = cl.map_shared_rank(sn, 0);
+  int* pi0 = cl.map_shared_rank(pi_, 0);
+  int* qi0 = cl.map_shared_rank(qi_, 0);
+  int* cnt0 = cl.map_shared_rank(cnt, 0);
+  const double* src = a + offs[b];
+  for (int e = gt; e < m * m; e += gn) {
+    A[e] = src[e];
+    Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
+  }
+  for (int i = tid; i < mp; i += nt) perm[i] = i;
+  if (crank == 0 && tid == 0) {
+    cnt[0] = 0;
+    cnt[1] = 0;
+    cnt[2] = 0;
+  }
+  cluster_barrier(cl);
+  const int nblk = half * (half + 1) / 2;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    // counter of this sweep: cnt[sweep % 3], zeroed one sweep ahead
+    if (crank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0;
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int i = gt; i < half; i += gn) {
+        int p = perm[i], q = perm[mp - 1 - i];
+        if (p > q) { int x = p; p = q; q = x; }
+        double c = 1.0, s = 0.0;
+        bool rot = false;
+        if (q < m) {
+          double apq = A[p * m + q];
+          if (apq != 0.0) {
+            double app = A[p * m + p], aqq = A[q * m + q];
+            double g = 100.0 * fabs(apq);
+            if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
+              double tau = (aqq - app) / (2.0 * apq);
+              double t = fabs(tau) > 1e150 ? 0.5 / tau
+                                           : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+              c = 1.0 / sqrt(1.0 + t * t);
+              s = t * c;
+              rot = true;
+            }
+          }
+        }
+        cs0[i] = c;
+        sn0[i] = s;
+        pi0[i] = p;
+        qi0[i] = (q < m) ? q : -1;
+        if (rot) atomicAdd(&cnt0[sweep % 3], 1);
+      }
+      cluster_barrier(cl);
+      if (crank != 0) {
+        for (int i = tid; i < half; i += nt) {
+          cs[i] = cs0[i];
+          sn[i] = sn0[i];
+          pi_[i] = pi0[i];
+          qi_[i] = qi0[i];
+        }
+      }
+      __syncthreads();
+      for (int e = gt; e < nblk; e += gn) {
+        int i, j;
+        unrank_upper(e, half, i, j);
+        const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+        if (si == 0.0 && sj == 0.0) continue;   // identity on this block: nothing changes
+        const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
+        if (q >= 0 && u >= 0) {
+          double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
+          double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
+          double b21 = si * app + ci * aqp, b22 = si * apq + ci * aqq;
+          double n11 = cj * b11 - sj * b12, n12 = sj * b11 + cj * b12;
+          double n21 = cj * b21 - sj * b22, n22 = sj * b21 + cj * b22;
+          if (i == j && si != 0.0) { n12 = 0.0; n21 = 0.0; }
+          A[p * m + r] = n11; A[p * m + u] = n12; A[q * m + r] = n21; A[q * m + u] = n22;
+          if (i != j) {
+            A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
+          }
+        } else if (q >= 0) {
+          double ap = A[p * m + r], aq = A[q * m + r];
+          double np = ci * ap - si * aq, nq = si * ap + ci * aq;
+          A[p * m + r] = np; A[q * m + r] = nq;
+          if (i != j) { A[r * m + p] = np; A[r * m + q] = nq; }
+        } else if (u >= 0) {
+          double ar = A[p * m + r], au = A[p * m + u];
+          double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
+          A[p * m + r] = nr; A[p * m + u] = nu;
+          if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
+        }
+      }
+      for (int i = gt >> 5; i < half; i += gn >> 5) {
+        const int p = pi_[i], q = qi_[i];
+        const double c = cs[i], s = sn[i];
+        if (q < 0 || s == 0.0) continue;
+        for (int k = gt & 31; k < m; k += 32) {
+          double vp = Vt[p * m + k], vq = Vt[q * m + k];
+          Vt[p * m + k] = c * vp - s * vq;
+          Vt[q * m + k] = s * vp + c * vq;
+        }
+      }
+      for (int i = tid; i < mp; i += nt)
+        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
+      __syncthreads();
+      for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
+      cluster_barrier(cl);
+    }
+    const int nrot = cnt0[sweep % 3];   // complete: every add precedes the last barrier
+    cluster_barrier(cl);                // everyone has read it before rank 0 reuses it
+    if (nrot == 0) break;
+  }
+  double* ev = evals + eoffs[b];
+  double* vec = evecs + offs[b];
+  for (int i = gt; i < m; i += gn) {
+    double di = A[i * m + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      double dj = A[j * m + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    ev[rank] = di;
+    for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = Vt[i * m + k];
+  }
+}
+
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s) {
+                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster) {
   if (n_mat <= 0) return;
+  const bool cluster = use_cluster && max_dim > kJacobiSmemAV;
   // the largest per-matrix need over every dimension up to max_dim
   size_t smem = 0;
-  for (int m = 1; m <= max_dim; ++m) smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr = smem;
+  const int single_max = cluster ? kJacobiSmemAV : max_dim;
+  for (int m = 1; m <= single_max; ++m)
+    smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
+  {
+    static std::mutex mu;
+    static size_t attr = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > attr) {
+      cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      attr = smem;
+    }
   }
-  k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs);
+  k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
+                                                cluster ? kJacobiSmemAV : INT_MAX);
+  g_launches += 1;
+  if (!cluster) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(n_mat) * kJacobiCluster, 1, 1);
+  cfg.blockDim = dim3(kJacobiThreads, 1, 1);
+  cfg.dynamicSmemBytes = jacobi_cluster_smem_bytes(max_dim);
+  cfg.stream = s;
+  cudaLaunchAttribute attr_c[1];
+  attr_c[0].id = cudaLaunchAttributeClusterDimension;
+  attr_c[0].val.clusterDim.x = kJacobiCluster;
+  attr_c[0].val.clusterDim.y = 1;
+  attr_c[0].val.clusterDim.z = 1;
+  cfg.attrs = attr_c;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs);
   g_launches += 1;
 }
 
@@ -510,12 +795,11 @@ void launch_select(int n, const double* vals, const int* sector, int n_sec, int 
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
   size_t smem = size_t(n2) * (sizeof(double) + sizeof(int));
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSelectMax * int(sizeof(double) + sizeof(int)));
-    attr = true;
-  }
+  });
   k_select<<<1, 1024, smem, s>>>(n, vals, sector, n_sec, M, cutoff, kept, out);
   g_launches += 1;
 }
@@ -684,18 +968,52 @@ void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_
 namespace b2k {
 
 __global__ void k_scale_cols(int m, const double* __restrict__ u, const double* __restrict__ lam,
-                             double power, double floor_, double* out) {
+                             double power, double floor_, int drop, double* out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     int c = e % m;
-    out[e] = u[e] * pow(fmax(lam[c], floor_), power);
+    const double l = lam[c];
+    out[e] = (drop && l < floor_) ? 0.0 : u[e] * pow(fmax(l, floor_), power);
   }
 }
 
 void launch_scale_cols(int m, const double* u, const double* lam, double power, double floor_,
-                       double* out, cudaStream_t s) {
+                       double* out, cudaStream_t s, bool drop_below) {
   int blocks = (m * m + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  k_scale_cols<<<blocks, 256, 0, s>>>(m, u, lam, power, floor_, out);
+  k_scale_cols<<<blocks, 256, 0, s>>>(m, u, lam, power, floor_, drop_below ? 1 : 0, out);
+  g_launches += 1;
+}
+
+}  // namespace b2k
+
+namespace b2k {
+
+__global__ void __launch_bounds__(256) k_dots(const DotOut* __restrict__ outs,
+                                              const DotTerm* __restrict__ terms,
+                                              const double* __restrict__ A,
+                                              const double* __restrict__ B, double* out) {
+  __shared__ double red[256];
+  const DotOut o = outs[blockIdx.x];
+  double acc = 0.0;
+  for (int t = o.t0; t < o.t1; ++t) {
+    const DotTerm d = terms[t];
+    double part = 0.0;
+    for (int e = threadIdx.x; e < d.n; e += 256) part = fma(A[d.offA + e], B[d.offB + e], part);
+    acc = fma(d.sign, part, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+void launch_dots(int n_out, const DotOut* outs, const DotTerm* terms, const double* A,
+                 const double* B, double* out, cudaStream_t s) {
+  if (n_out <= 0) return;
+  k_dots<<<n_out, 256, 0, s>>>(outs, terms, A, B, out);
   g_launches += 1;
 }
 

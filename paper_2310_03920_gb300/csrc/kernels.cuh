@@ -40,6 +40,19 @@ struct GemmTile {
   int out, r0, c0;
 };
 constexpr int kTile = 32;
+// Work item of the FP64 kernel: the 32 x 32 tile (r0, c0) of output out, summed over the
+// terms [t0, t1) of that output.  slot < 0: the item owns the tile and writes the output;
+// slot >= 0: the item is one of several term ranges of the tile and writes its partial sum
+// to partial[slot] (32 x 32), and a reduction task adds the slots in order.
+struct GemmTask {
+  int out, r0, c0;
+  int t0, t1;
+  int slot;
+};
+struct GemmReduce {
+  int out, r0, c0;
+  int slot0, n;
+};
 
 // out[i] (+)= sum_t c_t * in_t[i] for i < n: precombination of operator blocks.
 struct CombTerm {
@@ -78,8 +91,32 @@ struct CopyTask {
   uint8_t bsrc, bdst;
 };
 
-void launch_gemm(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                 const BufTable& bt, cudaStream_t s);
+void launch_gemm(const GemmTask* tasks, int n_tasks, const GemmReduce* reds, int n_reds,
+                 double* partial, const GemmOut* outs, const GemmTerm* terms, const BufTable& bt,
+                 cudaStream_t s);
+// One problem of a grouped launch (many independent problems in one grid): its work
+// items, reductions, outputs, terms, partial tiles and buffers; item0 / red0 are the
+// grid indices of its first work item / reduction (groups in increasing order).
+struct GemmGroup {
+  const GemmTask* tasks;
+  const GemmReduce* reds;
+  const GemmOut* outs;
+  const GemmTerm* terms;
+  double* partial;
+  BufTable bt;
+  int item0, red0;
+};
+void launch_gemm_grouped(const GemmGroup* groups, int n_groups, int n_items, int n_reds,
+                         cudaStream_t s);
+struct GemmGroupTc {
+  const GemmTile* tiles;
+  const GemmOut* outs;
+  const GemmTerm* terms;
+  BufTable bt;
+  int tile0;
+};
+void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
+                            cudaStream_t s);
 // Split-precision (bf16 hi/lo, three products, FP32 accumulation in TMEM) version of
 // launch_gemm on the tcgen05 tensor cores; tiles are kTcTile x kTcTile.  A bounded wait that
 // runs out writes 1 to *status.
@@ -94,10 +131,13 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 // Batched symmetric eigensolver; offs/eoffs: element offsets of each matrix (dims^2 each)
 // and of its eigenvalues; work/woffs: global work space of 2 dims^2 doubles for each
 // matrix with dims > kJacobiSmemAV (the smaller ones work in shared memory).
+// With use_cluster, matrices with dims > kJacobiSmemAV are solved by a cluster of
+// kJacobiCluster CTAs each (same rotations, same results), the others by one CTA each.
 constexpr int kJacobiSmemAV = 112;
+constexpr int kJacobiCluster = 8;
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s);
+                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true);
 // Global top-M selection over n eigenvalues (sector-major, descending in each sector).
 // sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
 // (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.
@@ -126,8 +166,22 @@ void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cud
 // Build the symmetric k x k Rayleigh matrix from the stored overlaps: g[i*k+j] =
 // 0.5 (VW[i][j] + VW[j][i]), VW row-major with stride kmax.
 void launch_symmetrize(int k, const double* vw, int kmax, double* g, cudaStream_t s);
-// out[r][c] = u[r][c] * max(lam[c], floor)^power for an m x m row-major matrix.
+// out[r][c] = u[r][c] * max(lam[c], floor)^power for an m x m row-major matrix; with
+// drop_below, columns with lam[c] < floor are set to zero instead.
 void launch_scale_cols(int m, const double* u, const double* lam, double power, double floor,
-                       double* out, cudaStream_t s);
+                       double* out, cudaStream_t s, bool drop_below = false);
+
+// out[k] = sum_t sign_t * dot(A[offA_t : +n_t], B[offB_t : +n_t]) over the tasks t of output k
+// (one CTA per output, fixed summation order).
+struct DotTerm {
+  int64_t offA, offB;
+  int n;
+  double sign;
+};
+struct DotOut {
+  int t0, t1;
+};
+void launch_dots(int n_out, const DotOut* outs, const DotTerm* terms, const double* A,
+                 const double* B, double* out, cudaStream_t s);
 
 }  // namespace b2k

@@ -1,5 +1,5 @@
 // MPO of the ab initio Hamiltonian (block2 paper, Sec. 2.1.1 for the Hamiltonian,
-// Sec. 3.2 for the automatic MPO construction from operator strings and the
+// Sec. 2.3 for the automatic MPO construction from operator strings and the
 // normal/complementary partition with the NC -> CN switch at the middle site).
 //
 // Every Hamiltonian term is rewritten as a site-ordered string of local operators (the
@@ -110,7 +110,14 @@ struct ElemOp {
 struct MpoBuilder {
   int n;
   OpTable table;
-  std::unordered_map<uint64_t, double> strings;   // packed string -> coefficient
+  // distinct site-ordered strings in first-seen order, with their summed coefficients
+  std::unordered_map<uint64_t, int> index;
+  std::vector<uint64_t> keys;
+  std::vector<double> coefs;
+  // for gradients: every spin-orbital term, its string and sign, and the integral it reads
+  std::vector<b2_mpo_s::TermRec> terms;
+  int cur_integral = 0;
+  int8_t cur_kind = 0;
 
   explicit MpoBuilder(int n_) : n(n_) {}
 
@@ -149,7 +156,19 @@ struct MpoBuilder {
       }
     }
     if (!flush()) return;
-    strings[s.pack(0, s.len)] += sign * coef;
+    const uint64_t key = s.pack(0, s.len);
+    auto it = index.find(key);
+    int idx;
+    if (it == index.end()) {
+      idx = int(keys.size());
+      index.emplace(key, idx);
+      keys.push_back(key);
+      coefs.push_back(0.0);
+    } else {
+      idx = it->second;
+    }
+    coefs[idx] += sign * coef;
+    terms.push_back({idx, cur_integral, cur_kind, int8_t(sign > 0 ? 1 : -1)});
   }
 
   static Str unpack(uint64_t k) {
@@ -210,6 +229,8 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
     for (int q = 0; q < n; ++q) {
       double v = h1[size_t(p) * n + q];
       if (std::abs(v) <= cutoff || v == 0) continue;
+      bld.cur_integral = p * n + q;
+      bld.cur_kind = 0;
       for (int s = 0; s < 2; ++s) {
         ops[0] = {2 * p + s, true};
         ops[1] = {2 * q + s, false};
@@ -222,6 +243,8 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
         for (int s = 0; s < n; ++s) {
           double v = eri[((size_t(p) * n + q) * n + r) * n + s];
           if (std::abs(v) <= cutoff || v == 0) continue;
+          bld.cur_integral = int(((p * n + q) * n + r) * n + s);
+          bld.cur_kind = 1;
           for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
               ops[0] = {2 * p + a, true};
@@ -283,18 +306,21 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
     return kTypeR | s.pack(split, s.len);
   };
 
-  for (const auto& kv : bld.strings) {
-    double coef = kv.second;
+  mpo->str_entry.assign(bld.keys.size(), b2_mpo_s::StringEntry{-1, -1, -1, -1});
+  for (size_t si = 0; si < bld.keys.size(); ++si) {
+    double coef = bld.coefs[si];
     if (coef == 0) continue;
-    b2::Str s = MpoBuilder::unpack(kv.first);
+    b2::Str s = MpoBuilder::unpack(bld.keys[si]);
     int first = s.site[0], last = s.site[s.len - 1];
     int el = 0;
     for (int k = first; k <= last; ++k) {
       uint64_t src_key = key_of(s, k), dst_key = key_of(s, k + 1);
       int src = chans[k].get(src_key), dst = chans[k + 1].get(dst_key);
       const double* mat = eye;
+      int op_id = -1;
       if (el < s.len && s.site[el] == k) {
-        mat = bld.table.mats[s.op[el]].data();
+        op_id = s.op[el];
+        mat = bld.table.mats[op_id].data();
         ++el;
       }
       bool src_plain = (src_key >> 62) == (kTypeI >> 62) || (src_key >> 62) == 0;
@@ -302,6 +328,7 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
       auto& e = entry(k, src, dst);
       if (src_plain && !dst_plain) {
         for (int i = 0; i < 16; ++i) e.m[i] += coef * mat[i];
+        mpo->str_entry[si] = {k, src, dst, op_id};   // where this string's coefficient enters
       } else {
         B2_REQUIRE(src_plain || !dst_plain, B2_EINVAL, "internal: channel order");
         for (int i = 0; i < 16; ++i) e.m[i] = mat[i];
@@ -332,6 +359,10 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
       mpo->dq[k][w] = (type == 0) ? q : QN{-q.n, -q.tsz};
     }
   }
+  mpo->terms = std::move(bld.terms);
+  mpo->ops.resize(bld.table.mats.size());
+  for (size_t i = 0; i < bld.table.mats.size(); ++i)
+    std::copy(bld.table.mats[i].begin(), bld.table.mats[i].end(), mpo->ops[i].begin());
   // drop W entries that cancelled exactly
   for (int k = 0; k < n; ++k) {
     auto& v = mpo->W[k];

@@ -21,6 +21,8 @@
 
 #include <cstdint>
 
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace b2k {
@@ -98,15 +100,17 @@ __device__ __forceinline__ void split(double x, __nv_bfloat16& hi, __nv_bfloat16
   lo = __float2bfloat16_rn(static_cast<float>(x - static_cast<double>(__bfloat162float(hi))));
 }
 
-// Stage op(M)[r0 + i][c0 + k] (i < rows_tile, k < 64; zero outside rows x cols) as the
-// K-major operand (row i, K index k), scaled by s, into hi/lo tiles.
+// Stage op(M)[r0 + i][c0 + k] (i < rows_tile, k < kw; zero outside rows x cols) as the
+// K-major operand (row i, K index k), scaled by s, into hi/lo tiles.  kw (a multiple of 16)
+// covers the K-steps the MMA will read; rows >= rows_tile are left as they are (zero).
 __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char* lo, const double* M,
                                                int ld, int rows, int cols, int r0, int c0,
-                                               bool trans, int rows_tile, double s, int tid) {
-  const int n = rows_tile * kKc;
+                                               bool trans, int rows_tile, int kw, double s,
+                                               int tid) {
+  const int n = rows_tile * kw;
   if (!trans) {
     for (int e = tid; e < n; e += 128) {
-      int i = e >> 6, k = e & 63;
+      int i = e / kw, k = e - i * kw;
       int r = r0 + i, c = c0 + k;
       double x = (r < rows && c < cols) ? s * M[int64_t(r) * ld + c] : 0.0;
       __nv_bfloat16 h, l;
@@ -117,7 +121,7 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
     }
   } else {
     for (int e = tid; e < n; e += 128) {
-      int k = e / rows_tile, i = e % rows_tile;
+      int k = e / rows_tile, i = e - k * rows_tile;
       int r = r0 + i, c = c0 + k;
       double x = (r < rows && c < cols) ? s * M[int64_t(c) * ld + r] : 0.0;
       __nv_bfloat16 h, l;
@@ -131,10 +135,9 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
 
 }  // namespace
 
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles,
-                                                 const GemmOut* __restrict__ outs,
-                                                 const GemmTerm* __restrict__ terms, BufTable bt,
-                                                 int* status) {
+__device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut* __restrict__ outs,
+                                             const GemmTerm* __restrict__ terms, const BufTable& bt,
+                                             int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -146,7 +149,6 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
   __shared__ uint32_t tmem_slot;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const GemmTile tile = tiles[blockIdx.x];
   const GemmOut o = outs[tile.out];
   const int r0 = tile.r0, c0 = tile.c0;
   const int nt = min(kCols, o.N - c0);
@@ -169,6 +171,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
   const uint32_t tmem_t = tmem, tmem_acc = tmem + 128;
   const uint32_t lane_off = uint32_t(warp * 32) << 16;
 
+  // rows of the A operand beyond the output block stay zero for every term
+  const int m_rows = min(kRows, o.M - r0);
+  for (int e = tid; e < kTileBytes / 16; e += 128) {
+    reinterpret_cast<uint4*>(a_hi)[e] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(a_lo)[e] = make_uint4(0, 0, 0, 0);
+  }
   uint32_t phase = 0;
   bool ok = true, started = false;
   const uint32_t ia = smem_u32(a_hi), ial = smem_u32(a_lo), ib = smem_u32(b_hi), ibl = smem_u32(b_lo);
@@ -204,9 +212,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
     if (g.flags & kTwoOp) {
       for (int k0 = 0; k0 < g.K1 && ok; k0 += kKc) {
         const int kc = min(kKc, g.K1 - k0);
-        stage_rowmajor(a_hi, a_lo, P, g.ldP, o.M, g.K1, r0, k0, tP, kRows, g.alpha, tid);
+        const int kw = ((kc + 15) / 16) * 16;
+        stage_rowmajor(a_hi, a_lo, P, g.ldP, o.M, g.K1, r0, k0, tP, m_rows, kw, g.alpha, tid);
         // B operand row n = output column c0 + n, K index k: op(X)[k0 + k][c0 + n]
-        stage_rowmajor(b_hi, b_lo, X, g.ldX, o.N, g.K1, c0, k0, !tQ, n_acc, 1.0, tid);
+        stage_rowmajor(b_hi, b_lo, X, g.ldX, o.N, g.K1, c0, k0, !tQ, n_acc, kw, 1.0, tid);
         ok = run_mma(tmem_acc, n_acc, (kc + 15) / 16, started);
         started = true;
       }
@@ -218,14 +227,15 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
         // T = op(P)[rows, :] X[:, k2:k2+64]
         for (int k1 = 0; k1 < g.K1 && ok; k1 += kKc) {
           const int kc1 = min(kKc, g.K1 - k1);
-          stage_rowmajor(a_hi, a_lo, P, g.ldP, o.M, g.K1, r0, k1, tP, kRows, 1.0, tid);
+          const int kw1 = ((kc1 + 15) / 16) * 16;
+          stage_rowmajor(a_hi, a_lo, P, g.ldP, o.M, g.K1, r0, k1, tP, m_rows, kw1, 1.0, tid);
           // B operand row n = column k2 + n of X, K index k = row k1 + k of X
-          stage_rowmajor(b_hi, b_lo, X, g.ldX, g.K2, g.K1, k2, k1, true, n_t, 1.0, tid);
+          stage_rowmajor(b_hi, b_lo, X, g.ldX, g.K2, g.K1, k2, k1, true, n_t, kw1, 1.0, tid);
           ok = run_mma(tmem_t, n_t, (kc1 + 15) / 16, k1 > 0);
         }
         if (!ok) break;
         // T (FP32, row = thread) -> alpha * T split into the A operand
-        {
+        if (warp * 32 < m_rows) {   // warps holding only rows past the block: T is zero there
           const int row = warp * 32 + lane;
           for (int cc = 0; cc < n_t; cc += 16) {
             float v[16];
@@ -239,16 +249,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
               *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
             }
           }
-          for (int cc = n_t; cc < kKc; cc += 16)
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              uint32_t off = koff(row, cc + j);
-              *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = __float2bfloat16_rn(0.f);
-              *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = __float2bfloat16_rn(0.f);
-            }
         }
         // B operand row n = output column c0 + n, K index k: op(Q)[k2 + k][c0 + n]
-        stage_rowmajor(b_hi, b_lo, Q, g.ldQ, o.N, g.K2, c0, k2, !tQ, n_acc, 1.0, tid);
+        stage_rowmajor(b_hi, b_lo, Q, g.ldQ, o.N, g.K2, c0, k2, !tQ, n_acc, n_t, 1.0, tid);
         ok = run_mma(tmem_acc, n_acc, (kc2 + 15) / 16, started);
         started = true;
       }
@@ -288,17 +291,50 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles,
+                                                 const GemmOut* __restrict__ outs,
+                                                 const GemmTerm* __restrict__ terms, BufTable bt,
+                                                 int* status) {
+  gemm_tc_item(tiles[blockIdx.x], outs, terms, bt, status);
+}
+
+// Grouped launch over several problems: CTA b takes tile b - tile0 of the group g with
+// tile0(g) <= b < tile0(g + 1).
+__global__ void __launch_bounds__(128) k_gemm_tc_grouped(const GemmGroupTc* __restrict__ groups,
+                                                         int n_groups, int* status) {
+  int lo = 0, hi = n_groups - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const GemmGroupTc& G = groups[lo];
+  const BufTable bt = G.bt;
+  gemm_tc_item(G.tiles[b - G.tile0], G.outs, G.terms, bt, status);
+}
+
 size_t gemm_tc_smem() { return size_t(4) * kTileBytes + 1024; }
 
 void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
                     const BufTable& bt, int* status, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
-    attr = true;
-  }
+  });
   k_gemm_tc<<<n_tiles, 128, gemm_tc_smem(), s>>>(tiles, outs, terms, bt, status);
+  count_launches(1);
+}
+
+void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
+                            cudaStream_t s) {
+  if (n_groups <= 0 || n_tiles <= 0) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_gemm_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(gemm_tc_smem()));
+  });
+  k_gemm_tc_grouped<<<n_tiles, 128, gemm_tc_smem(), s>>>(groups, n_groups, status);
   count_launches(1);
 }
 

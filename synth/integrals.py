@@ -76,7 +76,8 @@ def batch_problem(j):
     Draws the type (Hubbard or ab initio, 50/50), then for Hubbard the length L in
     [12, 40] and U in [1, 8], for ab initio the orbital count n in [10, 24] (integrals from
     ``ab_initio_integrals`` with the same seed), then the bond dimension M in [100, 800].
-    All at half filling, Sz = 0.  Returns a dict.
+    All at half filling with the lowest |Sz| (2Sz = 0, or 1 for an odd electron count).
+    Returns a dict.
     """
     rng = np.random.default_rng(1000 + j)
     kind = "hubbard" if rng.random() < 0.5 else "ab_initio"
@@ -90,5 +91,5 @@ def batch_problem(j):
         n = int(rng.integers(10, 25))
         M = int(rng.integers(100, 801))
         h, eri = ab_initio_integrals(n, seed=1000 + j)
-    return {"kind": kind, "n": n, "n_elec": n, "two_sz": 0, "M": M, "h": h, "eri": eri,
+    return {"kind": kind, "n": n, "n_elec": n, "two_sz": n % 2, "M": M, "h": h, "eri": eri,
             "seed": 1000 + j}

@@ -73,3 +73,17 @@ def test_static_eigh_rejects_requests_beyond_its_scratch():
     with pytest.raises(b2.B2Error):
         b2.b2_eigh_batched_static(ctx, [2] * 1025, a, ev, vec)
     ctx.close()
+
+
+def test_cluster_jacobi_matches_single_cta_bitwise():
+    # b2_eigh_batched solves matrices with dim > 112 on a CTA cluster; the static entry
+    # point keeps one CTA per matrix.  Both apply the same rotations in the same order.
+    ctx = b2.Context(0)
+    rng = np.random.default_rng(43)
+    dims = [113, 160, 201, 300]
+    mats, flat = _batch(rng, dims)
+    ev_c, vec_c = _run(b2.b2_eigh_batched, ctx, dims, flat)
+    ev_s, vec_s = _run(b2.b2_eigh_batched_static, ctx, dims, flat)
+    assert np.array_equal(ev_c, ev_s)
+    assert np.array_equal(vec_c, vec_s)
+    ctx.close()
