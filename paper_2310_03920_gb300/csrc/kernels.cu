@@ -46,6 +46,26 @@ __device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* 
   }
 }
 
+// acc[a][b] += sum_{kk < kn} A[2 ty + a][kk] * B[kk][4 tx + b], kn rounded up to 8 (the
+// tiles are zero there, so the sums equal the full-width ones exactly)
+__device__ __forceinline__ void tile_fma(const double (*As)[kTile + 1], const double (*Bs)[kTile + 1],
+                                         int kn, int tx, int ty, double (&acc)[2][4]) {
+  const int kn8 = (kn + 7) & ~7;
+  for (int k8 = 0; k8 < kn8; k8 += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int kk = k8 + u;
+      const double a0 = As[2 * ty][kk], a1 = As[2 * ty + 1][kk];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double x = Bs[kk][4 * tx + b];
+        acc[0][b] = fma(a0, x, acc[0][b]);
+        acc[1][b] = fma(a1, x, acc[1][b]);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* __restrict__ outs,
                                           const GemmTerm* __restrict__ terms, const BufTable& bt,
                                           double* __restrict__ partial) {
@@ -54,6 +74,8 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
   const GemmOut o = outs[tile.out];
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const int r0 = tile.r0, c0 = tile.c0;
+  // a warp owns tile rows 8w .. 8w+7: warps whose rows all lie past the block only load
+  const bool live = r0 + 8 * (tid >> 5) < o.M;
   double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   for (int t = tile.t0; t < tile.t1; ++t) {
     const GemmTerm g = terms[t];
@@ -66,16 +88,7 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
         load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k0, tP, tid);
         load_tile(Xs, X, g.ldX, g.K1, o.N, k0, c0, tQ, tid);
         __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < kTile; ++kk) {
-          double a0 = Ps[2 * ty][kk], a1 = Ps[2 * ty + 1][kk];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            double x = Xs[kk][4 * tx + b];
-            tacc[0][b] = fma(a0, x, tacc[0][b]);
-            tacc[1][b] = fma(a1, x, tacc[1][b]);
-          }
-        }
+        if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k0), tx, ty, tacc);
         __syncthreads();
       }
     } else {
@@ -86,16 +99,7 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
           load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k1, tP, tid);
           load_tile(Xs, X, g.ldX, g.K1, g.K2, k1, k2, false, tid);
           __syncthreads();
-#pragma unroll 8
-          for (int kk = 0; kk < kTile; ++kk) {
-            double a0 = Ps[2 * ty][kk], a1 = Ps[2 * ty + 1][kk];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              double x = Xs[kk][4 * tx + b];
-              tt[0][b] = fma(a0, x, tt[0][b]);
-              tt[1][b] = fma(a1, x, tt[1][b]);
-            }
-          }
+          if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k1), tx, ty, tt);
           __syncthreads();
         }
 #pragma unroll
@@ -105,16 +109,7 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
         }
         load_tile(Qs, Q, g.ldQ, g.K2, o.N, k2, c0, tQ, tid);
         __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < kTile; ++kk) {
-          double a0 = Ts[2 * ty][kk], a1 = Ts[2 * ty + 1][kk];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            double x = Qs[kk][4 * tx + b];
-            tacc[0][b] = fma(a0, x, tacc[0][b]);
-            tacc[1][b] = fma(a1, x, tacc[1][b]);
-          }
-        }
+        if (live) tile_fma(Ts, Qs, min(kTile, g.K2 - k2), tx, ty, tacc);
         __syncthreads();
       }
     }
@@ -299,12 +294,19 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 // blocks A[{p_i, q_i}][{p_j, q_j}] depend only on their own four entries, so a round is
 // one pass over the 2 x 2 blocks of the upper triangle (mirrored below), and the
 // eigenvector matrix is kept transposed (V^T) so that its rotations update two contiguous
-// rows.  A rotation is skipped when the off-diagonal element is negligible next to both
-// diagonal entries (100|a_pq| adds nothing to |a_pp| nor |a_qq|); the iteration stops after
-// a sweep without rotations (at most kMaxSweeps sweeps).  A lives in shared memory for
+// rows.  A rotation is skipped when the off-diagonal element is below kJacobiAbsTol times
+// the largest input element or negligible next to both diagonal entries (100|a_pq| adds
+// nothing to |a_pp| nor |a_qq|); the iteration stops after a sweep without rotations (at
+// most kMaxSweeps sweeps).  A lives in shared memory for
 // dim <= kJacobiSmemA, V^T too for dim <= kJacobiSmemAV; larger matrices use global work
 // space (2 dim^2 doubles).
 constexpr int kJacobiSmemA = 160;
+// A rotation is skipped when |a_pq| <= kJacobiAbsTol * max |a_ij| of the input: the
+// eigen-decomposition is then accurate to about that fraction of the largest element
+// (the accuracy of a backward-stable solver), and graded or rank-deficient density
+// matrices, whose smallest eigenvalues are rounding noise, stop after 10-15 sweeps instead
+// of chasing that noise up to kMaxSweeps.
+constexpr double kJacobiAbsTol = 1e-15;
 constexpr int kMaxSweeps = 60;
 constexpr int kJacobiThreads = 512;
 
@@ -318,6 +320,20 @@ __host__ __device__ inline size_t jacobi_smem_bytes(int m) {
   else if (m <= kJacobiSmemA)
     mat = size_t(m) * m * sizeof(double);
   return mat + aux;
+}
+
+// max |src[e]| over e < n, returned to every thread of the block (red: >= 32 doubles)
+__device__ double block_max_abs(const double* __restrict__ src, int n, double* red) {
+  double v = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) v = fmax(v, fabs(src[e]));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = 0.0;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+  __syncthreads();
+  return v;
 }
 
 // row-major rank e of the upper triangle (i <= j < half) -> (i, j); the float estimate
@@ -371,7 +387,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
     Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
   }
   for (int i = tid; i < mp; i += nt) perm[i] = i;
-  __syncthreads();
+  __shared__ double red[kJacobiThreads / 32];
+  const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);
   const int nblk = half * (half + 1) / 2;   // upper-triangle 2x2 blocks (i <= j)
   for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
     if (tid == 0) nrot = 0;
@@ -384,7 +401,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
         bool rot = false;
         if (q < m) {
           double apq = A[p * m + q];
-          if (apq != 0.0) {
+          if (fabs(apq) > tol) {
             double app = A[p * m + p], aqq = A[q * m + q];
             double g = 100.0 * fabs(apq);
             if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
@@ -480,10 +497,9 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
 // sees the same operations in the same order as in k_jacobi, so the results are identical.
 // One cluster per matrix: the grid is n_mat clusters, clusters of small matrices return at
 // once (uniformly, before any cluster barrier).
-__device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) {
-  __threadfence();
-  cl.sync();
-}
+// barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
+// and distributed-shared-memory accesses of the cluster's threads around the barrier
+__device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { cl.sync(); }
 
 __host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
   const int mp = m + (m & 1), half = mp / 2;
@@ -526,6 +542,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
   }
   for (int i = tid; i < mp; i += nt) perm[i] = i;
+  __shared__ double red[kJacobiThreads / 32];
+  const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);   // same in every CTA
   if (crank == 0 && tid == 0) {
     cnt[0] = 0;
     cnt[1] = 0;
@@ -544,7 +562,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
         bool rot = false;
         if (q < m) {
           double apq = A[p * m + q];
-          if (apq != 0.0) {
+          if (fabs(apq) > tol) {
             double app = A[p * m + p], aqq = A[q * m + q];
             double g = 100.0 * fabs(apq);
             if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {

@@ -2,7 +2,8 @@
 //
 // Same task lists as the FP64 kernel (kernels.cuh): each output block receives
 //   3-operand terms  alpha * op(P) X op(Q)      or   2-operand terms  alpha * op(P) op(X).
-// Every FP64 operand element a is split into bf16 hi = bf16(a) and lo = bf16(a - hi); a
+// Every FP64 operand element a is split into bf16 hi = bf16(a) and lo = bf16(a - hi) (formed
+// in FP32 after one rounding of a to FP32, see split()); a
 // product a*b is formed as hi*hi + hi*lo + lo*hi on the tensor cores with FP32
 // accumulation in tensor memory (TMEM); the FP32 tile is added to the FP64 output at the
 // end.  One CTA (4 warps) owns a 128 x 128 output tile:
@@ -95,9 +96,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void split(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(static_cast<float>(x));
-  lo = __float2bfloat16_rn(static_cast<float>(x - static_cast<double>(__bfloat162float(hi))));
+// hi = bf16(x), lo = bf16(x - hi), formed in FP32: x is rounded to FP32 once (relative
+// error 2^-24, far below the 2^-17 that hi + lo resolves), then f - hi is exact in FP32.
+// GB300's FP64 pipe is narrow, so the staging loops keep FP64 work to the one conversion.
+__device__ __forceinline__ void split(float f, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(f);
+  lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
 // Stage op(M)[r0 + i][c0 + k] (i < rows_tile, k < kw; zero outside rows x cols) as the
@@ -108,11 +112,12 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
                                                bool trans, int rows_tile, int kw, double s,
                                                int tid) {
   const int n = rows_tile * kw;
+  const float sf = static_cast<float>(s);
   if (!trans) {
     for (int e = tid; e < n; e += 128) {
       int i = e / kw, k = e - i * kw;
       int r = r0 + i, c = c0 + k;
-      double x = (r < rows && c < cols) ? s * M[int64_t(r) * ld + c] : 0.0;
+      const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(r) * ld + c]) : 0.f;
       __nv_bfloat16 h, l;
       split(x, h, l);
       uint32_t o = koff(i, k);
@@ -123,7 +128,7 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
     for (int e = tid; e < n; e += 128) {
       int k = e / rows_tile, i = e - k * rows_tile;
       int r = r0 + i, c = c0 + k;
-      double x = (r < rows && c < cols) ? s * M[int64_t(c) * ld + r] : 0.0;
+      const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(c) * ld + r]) : 0.f;
       __nv_bfloat16 h, l;
       split(x, h, l);
       uint32_t o = koff(i, k);
@@ -237,13 +242,14 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
         // T (FP32, row = thread) -> alpha * T split into the A operand
         if (warp * 32 < m_rows) {   // warps holding only rows past the block: T is zero there
           const int row = warp * 32 + lane;
+          const float af = static_cast<float>(g.alpha);
           for (int cc = 0; cc < n_t; cc += 16) {
             float v[16];
             tmem_ld16(tmem_t + lane_off + uint32_t(cc), v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               __nv_bfloat16 h, l;
-              split(g.alpha * double(v[j]), h, l);
+              split(af * v[j], h, l);
               uint32_t off = koff(row, cc + j);
               *reinterpret_cast<__nv_bfloat16*>(a_hi + off) = h;
               *reinterpret_cast<__nv_bfloat16*>(a_lo + off) = l;
