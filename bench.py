@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "window_M1000", "window_M2000", "batch64"],
+                    choices=["sweep", "window_M1000", "window_M2000", "batch64", "grad_n24"],
                     help="sweep: Hubbard L=32 M=500 full sweep (default); window_M*: middle "
                          "window of the n=36 ab initio system, FP64 vs split precision; "
-                         "batch64: 64 independent problems, grouped vs one-by-one launches")
+                         "batch64: 64 independent problems, grouped vs one-by-one launches; "
+                         "grad_n24: integral gradient (1- and 2-RDM) at n=24, M=500")
     ap.add_argument("--batch", type=int, default=64, help="problems of the batch64 workload")
     ap.add_argument("--davidson", action="store_true",
                     help="window_M*: also solve the window (split precision to |r|^2 <= 1e-7, "
@@ -431,6 +432,51 @@ def run_batch(args):
     ctx.close()
 
 
+def run_grad(args):
+    """Integral gradient dE/dh, dE/d(pq|rs) (spin-traced 1- and 2-RDM) of an n = 24,
+    N = 24 ab initio MPS at M = 500 (random MPS from the sector recipe, seeded): times
+    b2_rdm_grad end to end (gradient MPO build, environments, one-site adjoints, Jacobian)
+    and checks E = e_core + h.gamma + 1/2 eri.Gamma against <psi|H|psi> from H_eff."""
+    import numpy as np
+    import torch
+    from paper_2310_03920_gb300 import b2
+    from synth import ab_initio_integrals
+    n, N, M = 24, 24, 500
+    h, eri = ab_initio_integrals(n, seed=24)
+    ctx = b2.Context(0)
+    mpo = b2.b2_build_mpo(ctx, h, eri, 0.0, N, 0)
+    mps = b2.b2_mps_random(ctx, mpo, M, seed=124)
+    b2.b2_rdm_grad(ctx, mpo, mps, n)                # warm-up (kernel attributes, allocator)
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g1, g2 = b2.b2_rdm_grad(ctx, mpo, mps, n)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    env = b2.b2_env_init(ctx, mpo, mps, 0)
+    nel, _ = b2.b2_psi_layout(ctx, env, 0)
+    psi = torch.empty(nel, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(psi)
+    b2.b2_psi_from_mps(ctx, env, 0, psi)
+    b2.b2_heff_apply(ctx, env, 0, psi, out)
+    torch.cuda.synchronize()
+    e_env = float(torch.dot(psi, out) / torch.dot(psi, psi))
+    e_rdm = float(np.sum(h * g1) + np.sum(eri * g2))
+    sec = float(np.median(times))
+    line = {"metric": METRIC, "value": sec, "unit": "s per gradient", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "abinitio_n24_N24_M500_rdm_gradient", "n": n, "n_elec": N, "M": M},
+            "gradient_elements": n * n + n ** 4, "energy_identity_abs_err": abs(e_env - e_rdm),
+            "trace_gamma": float(np.trace(g1))}
+    print(json.dumps(line), flush=True)
+    b2.b2_free_env(env)
+    b2.b2_free_mps(mps)
+    b2.b2_free_mpo(mpo)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -439,6 +485,9 @@ def main():
         return
     if args.workload == "batch64":
         run_batch(args)
+        return
+    if args.workload == "grad_n24":
+        run_grad(args)
         return
     if args.workload != "sweep":
         run_window(args)

@@ -241,8 +241,9 @@ int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts*
 
 /* ------------------------------------------------------------------ batched eigensolver
  * Eigen-decomposition of n_mat real symmetric matrices by cyclic Jacobi rotations in
- * FP64 (one thread block per matrix of dim <= 112, a cluster of 8 thread blocks per larger
- * matrix, same results): the density-matrix step of the truncation.  Rotations stop once
+ * FP64 (one thread block per matrix of dim <= 64, a cluster of 16 thread blocks -- 8 where
+ * the device cannot run 16 -- per larger matrix, same results): the density-matrix step of
+ * the truncation.  Rotations stop once
  * every off-diagonal element is below 1e-15 times the largest input element (or negligible
  * next to its diagonal entries): eigenvalues and eigenvectors are accurate to about that
  * fraction of the largest element, as from a backward-stable solver.

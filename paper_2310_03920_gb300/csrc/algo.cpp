@@ -268,7 +268,7 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     eoffs[j] = secs[j].eoff;
     tot_e += dims[j];
     max_dim = std::max(max_dim, dims[j]);
-    if (dims[j] > b2k::kJacobiSmemAV) {
+    if (b2k::jacobi_needs_work(dims[j])) {
       woffs[j] = tot_w;
       tot_w += 2 * int64_t(dims[j]) * dims[j];
     }

@@ -294,7 +294,7 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
       eoffs[i] = e;
       o += int64_t(d[i]) * d[i];
       e += d[i];
-      if (d[i] > b2k::kJacobiSmemAV) {
+      if (b2k::jacobi_needs_work(d[i])) {
         woffs[i] = w;
         w += 2 * int64_t(d[i]) * d[i];
       }

@@ -67,7 +67,7 @@ void gram_factors(Ctx* c, const std::vector<int>& dims, const std::vector<int64_
   for (size_t j = 0; j < dims.size(); ++j) {
     B2_REQUIRE(dims[j] <= 1024, B2_EUNSUPPORTED, "gradient: bond sector larger than 1024 states");
     max_dim = std::max(max_dim, dims[j]);
-    if (dims[j] > b2k::kJacobiSmemAV) {
+    if (b2k::jacobi_needs_work(dims[j])) {
       woff[j] = wsize;
       wsize += 2 * int64_t(dims[j]) * dims[j];
     }

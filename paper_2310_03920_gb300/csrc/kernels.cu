@@ -336,6 +336,38 @@ __device__ double block_max_abs(const double* __restrict__ src, int n, double* r
   return v;
 }
 
+// Rotation (c, s) annihilating a_pq of the 2 x 2 pivot [app apq; apq aqq] (the smaller of
+// the two angles, t = tan = s / c the root of apq t^2 + (aqq - app) t - apq = 0 with
+// |t| <= 1).  FP64 division and square root are long dependent chains on GB300's narrow
+// FP64 pipe and sat on the critical path of every round, so t starts from FP32 arithmetic
+// and is refined by two Newton steps in FP64 whose divisor is an FP32 reciprocal of the
+// derivative (each step multiplies the error by ~1e-7), and c = (1 + t^2)^(-1/2) starts
+// from an FP32 reciprocal square root refined by two FP64 Newton steps y(3 - x y^2)/2: the
+// rotation equals the exactly computed one to rounding and is orthogonal to rounding.  The
+// pivot is scaled by a power of two first, so that FP32 neither overflows nor underflows.
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& c,
+                                                double& s) {
+  const double d = aqq - app;
+  const int ex = max(ilogb(fmax(fabs(d), fabs(apq))), -1000);
+  const double ds = scalbn(d, -ex), ps = scalbn(apq, -ex);
+  const float tau = static_cast<float>(ds) / (2.0f * static_cast<float>(ps));
+  const float t32 = fabsf(tau) > 1e18f ? 0.5f / tau
+                                        : copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  double t = t32;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double f = fma(fma(ps, t, ds), t, -ps);
+    const double r = 1.0f / static_cast<float>(fma(2.0 * ps, t, ds));
+    t = fma(-f, r, t);
+  }
+  const double x = fma(t, t, 1.0);
+  double y = rsqrtf(static_cast<float>(x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-0.5 * x * y, y, 1.5);
+  c = y;
+  s = t * y;
+}
+
 // row-major rank e of the upper triangle (i <= j < half) -> (i, j); the float estimate
 // is corrected with exact integer arithmetic
 __device__ __forceinline__ void unrank_upper(int e, int half, int& i, int& j) {
@@ -405,11 +437,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
             double app = A[p * m + p], aqq = A[q * m + q];
             double g = 100.0 * fabs(apq);
             if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
-              double tau = (aqq - app) / (2.0 * apq);
-              double t = fabs(tau) > 1e150 ? 0.5 / tau
-                                           : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-              c = 1.0 / sqrt(1.0 + t * t);
-              s = t * c;
+              jacobi_rotation(app, aqq, apq, c, s);
               rot = true;
             }
           }
@@ -488,13 +516,13 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
   }
 }
 
-// The same rotation sequence for one large matrix (dim > kJacobiSmemAV) spread over a
-// cluster of kJacobiCluster CTAs: GB300's FP64 rate per SM is low, so one SM per large
-// matrix bounds the whole truncation.  A and V^T stay in the global work space (L2
-// resident); every round, the cluster's threads compute the rotations of disjoint pairs
-// into rank 0's shared memory, synchronise, copy them to their own shared memory and
-// update disjoint 2 x 2 blocks of A and rows of V^T, then synchronise again.  Each element
-// sees the same operations in the same order as in k_jacobi, so the results are identical.
+// The same rotation sequence for one large matrix (dim > kJacobiClusterMin) spread over a
+// cluster of CTAs: GB300's FP64 rate per SM is low, so one SM per large matrix bounds the
+// whole truncation.  A and V^T stay in the global work space (L2 resident); every round,
+// each CTA computes all the round's rotations from A into its own shared memory (identical
+// in every CTA), the cluster synchronises, the CTAs update disjoint 2 x 2 blocks of A and
+// rows of V^T, and the cluster synchronises again.  Each element sees the same operations
+// in the same order as in k_jacobi, so the results are identical.
 // One cluster per matrix: the grid is n_mat clusters, clusters of small matrices return at
 // once (uniformly, before any cluster barrier).
 // barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
@@ -503,8 +531,7 @@ __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { c
 
 __host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
   const int mp = m + (m & 1), half = mp / 2;
-  return size_t(half) * (2 * sizeof(double) + 2 * sizeof(int)) + size_t(mp) * 2 * sizeof(int) +
-         4 * sizeof(int);
+  return size_t(half) * (2 * sizeof(double) + 2 * sizeof(int)) + size_t(mp) * 2 * sizeof(int);
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
@@ -517,7 +544,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   const int crank = int(cl.block_rank());
   const int b = blockIdx.x / C;
   const int m = dims[b];
-  if (m <= kJacobiSmemAV) return;   // whole cluster: handled by k_jacobi
+  if (m <= kJacobiClusterMin) return;   // whole cluster: handled by k_jacobi
   const int tid = threadIdx.x, nt = blockDim.x;
   const int gt = crank * nt + tid, gn = C * nt;
   const int mp = m + (m & 1), half = mp / 2;
@@ -529,13 +556,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   int* qi_ = pi_ + half;
   int* perm = qi_ + half;
   int* perm2 = perm + mp;
-  int* cnt = perm2 + mp;
-  // rank 0's arrays are the exchange area
-  double* cs0 = cl.map_shared_rank(cs, 0);
-  double* sn0 = cl.map_shared_rank(sn, 0);
-  int* pi0 = cl.map_shared_rank(pi_, 0);
-  int* qi0 = cl.map_shared_rank(qi_, 0);
-  int* cnt0 = cl.map_shared_rank(cnt, 0);
+  __shared__ int nrot;
   const double* src = a + offs[b];
   for (int e = gt; e < m * m; e += gn) {
     A[e] = src[e];
@@ -544,18 +565,15 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   for (int i = tid; i < mp; i += nt) perm[i] = i;
   __shared__ double red[kJacobiThreads / 32];
   const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);   // same in every CTA
-  if (crank == 0 && tid == 0) {
-    cnt[0] = 0;
-    cnt[1] = 0;
-    cnt[2] = 0;
-  }
   cluster_barrier(cl);
   const int nblk = half * (half + 1) / 2;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    // counter of this sweep: cnt[sweep % 3], zeroed one sweep ahead
-    if (crank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0;
+    if (tid == 0) nrot = 0;
+    __syncthreads();
     for (int round = 0; round < mp - 1; ++round) {
-      for (int i = gt; i < half; i += gn) {
+      // every CTA computes all rotations of the round from the same (global) A: the same
+      // values in every CTA, no exchange between them
+      for (int i = tid; i < half; i += nt) {
         int p = perm[i], q = perm[mp - 1 - i];
         if (p > q) { int x = p; p = q; q = x; }
         double c = 1.0, s = 0.0;
@@ -566,30 +584,19 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
             double app = A[p * m + p], aqq = A[q * m + q];
             double g = 100.0 * fabs(apq);
             if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
-              double tau = (aqq - app) / (2.0 * apq);
-              double t = fabs(tau) > 1e150 ? 0.5 / tau
-                                           : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-              c = 1.0 / sqrt(1.0 + t * t);
-              s = t * c;
+              jacobi_rotation(app, aqq, apq, c, s);
               rot = true;
             }
           }
         }
-        cs0[i] = c;
-        sn0[i] = s;
-        pi0[i] = p;
-        qi0[i] = (q < m) ? q : -1;
-        if (rot) atomicAdd(&cnt0[sweep % 3], 1);
+        cs[i] = c;
+        sn[i] = s;
+        pi_[i] = p;
+        qi_[i] = (q < m) ? q : -1;
+        if (rot) atomicAdd(&nrot, 1);
       }
+      // every CTA has read the pivots of this round before any CTA updates A
       cluster_barrier(cl);
-      if (crank != 0) {
-        for (int i = tid; i < half; i += nt) {
-          cs[i] = cs0[i];
-          sn[i] = sn0[i];
-          pi_[i] = pi0[i];
-          qi_[i] = qi0[i];
-        }
-      }
       __syncthreads();
       for (int e = gt; e < nblk; e += gn) {
         int i, j;
@@ -636,9 +643,9 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
       for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
       cluster_barrier(cl);
     }
-    const int nrot = cnt0[sweep % 3];   // complete: every add precedes the last barrier
-    cluster_barrier(cl);                // everyone has read it before rank 0 reuses it
+    // the count is the same in every CTA (same rotations), so the exit is uniform
     if (nrot == 0) break;
+    __syncthreads();
   }
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
@@ -658,10 +665,10 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster) {
   if (n_mat <= 0) return;
-  const bool cluster = use_cluster && max_dim > kJacobiSmemAV;
+  const bool cluster = use_cluster && max_dim > kJacobiClusterMin;
   // the largest per-matrix need over every dimension up to max_dim
   size_t smem = 0;
-  const int single_max = cluster ? kJacobiSmemAV : max_dim;
+  const int single_max = cluster ? kJacobiClusterMin : max_dim;
   for (int m = 1; m <= single_max; ++m)
     smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
   {
@@ -674,17 +681,44 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
     }
   }
   k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
-                                                cluster ? kJacobiSmemAV : INT_MAX);
+                                                cluster ? kJacobiClusterMin : INT_MAX);
   g_launches += 1;
   if (!cluster) return;
+  // 16 CTAs per cluster where the device runs such clusters, else the portable 8
+  static std::once_flag once;
+  static int csize = 8;
+  std::call_once(once, [] {
+    if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(16, 1, 1);
+    q.blockDim = dim3(kJacobiThreads, 1, 1);
+    q.dynamicSmemBytes = jacobi_cluster_smem_bytes(1024);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    q.attrs = at;
+    q.numAttrs = 1;
+    int n_clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&n_clusters, k_jacobi_cluster, &q) == cudaSuccess &&
+        n_clusters > 0)
+      csize = 16;
+    cudaGetLastError();
+  });
+  const int kc = csize;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(n_mat) * kJacobiCluster, 1, 1);
+  cfg.gridDim = dim3(unsigned(n_mat) * kc, 1, 1);
   cfg.blockDim = dim3(kJacobiThreads, 1, 1);
   cfg.dynamicSmemBytes = jacobi_cluster_smem_bytes(max_dim);
   cfg.stream = s;
   cudaLaunchAttribute attr_c[1];
   attr_c[0].id = cudaLaunchAttributeClusterDimension;
-  attr_c[0].val.clusterDim.x = kJacobiCluster;
+  attr_c[0].val.clusterDim.x = kc;
   attr_c[0].val.clusterDim.y = 1;
   attr_c[0].val.clusterDim.z = 1;
   cfg.attrs = attr_c;

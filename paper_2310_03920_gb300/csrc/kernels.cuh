@@ -130,11 +130,15 @@ void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const do
 void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s);
 // Batched symmetric eigensolver; offs/eoffs: element offsets of each matrix (dims^2 each)
 // and of its eigenvalues; work/woffs: global work space of 2 dims^2 doubles for each
-// matrix with dims > kJacobiSmemAV (the smaller ones work in shared memory).
-// With use_cluster, matrices with dims > kJacobiSmemAV are solved by a cluster of
-// kJacobiCluster CTAs each (same rotations, same results), the others by one CTA each.
+// matrix with jacobi_needs_work(dims, use_cluster) (the others work in shared memory).
+// With use_cluster, matrices with dims > kJacobiClusterMin are solved by a cluster of 16
+// CTAs (8 where the device cannot run 16) each, with the same rotations and results as
+// one CTA; the others by one CTA each.
 constexpr int kJacobiSmemAV = 112;
-constexpr int kJacobiCluster = 8;
+constexpr int kJacobiClusterMin = 64;
+inline bool jacobi_needs_work(int dim, bool use_cluster = true) {
+  return dim > (use_cluster ? kJacobiClusterMin : kJacobiSmemAV);
+}
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true);

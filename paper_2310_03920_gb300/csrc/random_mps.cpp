@@ -228,7 +228,7 @@ b2_mps_s* b2_mps_random_impl(b2::Ctx* ctx, b2_mpo_s* mpo, int M, const double* o
     int max_dim = 0;
     for (int j = 0; j < bl.size(); ++j) {
       max_dim = std::max(max_dim, dims[j]);
-      if (dims[j] > b2k::kJacobiSmemAV) {
+      if (b2k::jacobi_needs_work(dims[j])) {
         woff[j] = wsize;
         wsize += 2 * int64_t(dims[j]) * dims[j];
       }

@@ -76,11 +76,11 @@ def test_static_eigh_rejects_requests_beyond_its_scratch():
 
 
 def test_cluster_jacobi_matches_single_cta_bitwise():
-    # b2_eigh_batched solves matrices with dim > 112 on a CTA cluster; the static entry
+    # b2_eigh_batched solves matrices with dim > 64 on a CTA cluster; the static entry
     # point keeps one CTA per matrix.  Both apply the same rotations in the same order.
     ctx = b2.Context(0)
     rng = np.random.default_rng(43)
-    dims = [113, 160, 201, 300]
+    dims = [64, 65, 90, 112, 113, 160, 201, 300]
     mats, flat = _batch(rng, dims)
     ev_c, vec_c = _run(b2.b2_eigh_batched, ctx, dims, flat)
     ev_s, vec_s = _run(b2.b2_eigh_batched_static, ctx, dims, flat)
