@@ -296,14 +296,17 @@ int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every
- * launch of the H_eff contraction kernel is bracketed by CUDA events on the context
- * stream, and every kernel launch of the library is counted.  b2_profile(ctx, 1) also
- * resets the counters. */
+ * launch of the H_eff contraction kernel and of the truncation eigensolver is bracketed by
+ * CUDA events on the context stream, and every kernel launch of the library is counted.
+ * b2_profile(ctx, 1) also resets the counters. */
 typedef struct {
   int64_t launches;        /* kernel launches of the library since the reset */
   int64_t heff_launches;   /* H_eff contraction kernel launches timed */
   double heff_ms;          /* their summed device time */
   double heff_flops;       /* their summed algorithmic flops */
+  int64_t eig_launches;    /* truncation eigensolver calls timed (one or two kernels each) */
+  double eig_ms;           /* their summed device time */
+  double eig_flops;        /* 18 m flops per applied Jacobi rotation of an m x m block */
 } b2_profile_data;
 int b2_profile(b2_ctx ctx, int enable);
 int b2_profile_read(b2_ctx ctx, b2_profile_data* out);

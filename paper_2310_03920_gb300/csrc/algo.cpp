@@ -100,7 +100,7 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
   double* evecs = G + kmax * kmax;
   double* evals = evecs + kmax * kmax;
   double* cvec = evals + kmax;
-  double* scal = cvec + 2 * kmax;    // [0] |r|^2, [1] |t|^2, [2] norm of input
+  double* scal = cvec + 2 * kmax;    // [0] |r|^2, [1] |t|^2, [2] norm of input, [3] breakdown
   DevBuf meta(c, sizeof(int64_t) * 4);
   double* Vp = V.as<double>();
   double* Wp = W.as<double>();
@@ -122,24 +122,42 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
   }
   b2k::launch_multidot(1, Vp, n, Wp, n, part, VW, 1, c->stream);
   // small eigensolver metadata: dims / offsets for the single k x k problem
-  int dims_h[1];
+  // (dims: a table 0..kmax on the device, so that no copy is needed per iteration)
+  std::vector<int> dims_h(kmax + 1);
+  for (int i = 0; i <= kmax; ++i) dims_h[i] = i;
   int64_t offs_h[2] = {0, 0};
-  DevBuf d_dims(c, sizeof(int)), d_offs(c, sizeof(int64_t) * 2);
+  DevBuf d_dims, d_offs(c, sizeof(int64_t) * 2);
+  upload(c, d_dims, dims_h);
   B2_CUDA(cudaMemcpyAsync(d_offs.ptr, offs_h, sizeof(offs_h), cudaMemcpyHostToDevice, c->stream));
+  // The extension of the basis is not checked on the host: a correction of norm < 1e-14
+  // (breakdown) is zeroed on the device and flags scal[3]; the flag is read with the
+  // residual of the next Rayleigh-Ritz step, which is then redone without that vector.
+  // One host synchronisation per iteration instead of two.
+  B2_CUDA(cudaMemsetAsync(scal + 3, 0, sizeof(double), c->stream));
   double host_sc[2];
+  double brk = 0;
+  bool stop_after_ritz = false;
   for (;;) {
     b2k::launch_symmetrize(k, VW, kmax, G, c->stream);
-    dims_h[0] = k;
-    B2_CUDA(cudaMemcpyAsync(d_dims.ptr, dims_h, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    b2k::launch_jacobi(1, d_dims.as<int>(), d_offs.as<int64_t>(), d_offs.as<int64_t>(), G, evals,
-                       evecs, nullptr, d_offs.as<int64_t>(), k, c->stream);
+    b2k::launch_jacobi(1, d_dims.as<int>() + k, d_offs.as<int64_t>(), d_offs.as<int64_t>(), G,
+                       evals, evecs, nullptr, d_offs.as<int64_t>(), k, c->stream);
     // lowest Ritz pair: last of the descending eigenvalues, column k-1
     b2k::launch_ritz(k, Vp, Wp, n, evecs + (k - 1), k, evals + (k - 1), diag.as<double>(),
                      u.as<double>(), hu.as<double>(), t.as<double>(), n, part, scal, c->stream);
     B2_CUDA(cudaMemcpyAsync(host_sc, scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     B2_CUDA(cudaMemcpyAsync(&res.energy, evals + (k - 1), sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream));
+    B2_CUDA(cudaMemcpyAsync(&brk, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     sync(c);
+    if (brk != 0.0) {   // the last vector added was a breakdown: drop it, redo Rayleigh-Ritz
+      --k;
+      --nmv;
+      res.flops -= fl;
+      brk = 0.0;
+      B2_CUDA(cudaMemsetAsync(scal + 3, 0, sizeof(double), c->stream));
+      stop_after_ritz = true;
+      continue;
+    }
     res.resid2 = host_sc[0];
     if (std::getenv("B2_TRACE_DAVIDSON"))
       std::fprintf(stderr, "davidson site %d k %d nmv %d theta %.15f r2 %.3e\n", site, k, nmv,
@@ -148,7 +166,7 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
                "Davidson produced a non-finite value");
     if (mv_prec != B2_FP64)
       B2_REQUIRE(c->take_status() == 0, B2_ETIMEOUT, "tensor-core wait ran out");
-    if (res.resid2 <= tol || nmv >= max_iter) break;
+    if (stop_after_ritz || res.resid2 <= tol || nmv >= max_iter) break;
     if (k >= kmax) {   // restart from the Ritz vector
       B2_CUDA(cudaMemcpyAsync(Vp, u.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
       B2_CUDA(cudaMemcpyAsync(Wp, hu.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -161,13 +179,10 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
       b2k::launch_multiaxpy(k, Vp, n, cvec, tp, n, -1.0, c->stream);
     }
     b2k::launch_multidot(1, tp, n, tp, n, part, scal + 1, 1, c->stream);
-    B2_CUDA(cudaMemcpyAsync(host_sc + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    sync(c);
-    if (!(std::sqrt(host_sc[1]) >= 1e-14)) break;
     double* vk = Vp + int64_t(k) * n;
     double* wk = Wp + int64_t(k) * n;
     B2_CUDA(cudaMemcpyAsync(vk, tp, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
-    b2k::launch_scale_inv_sqrt(vk, n, scal + 1, c->stream);
+    b2k::launch_scale_inv_sqrt(vk, n, scal + 1, c->stream, scal + 3);
     heff_apply(env, site, vk, wk, 0.0, &fl, mv_prec);
     res.flops += fl;
     ++nmv;
@@ -293,9 +308,20 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
   upload(c, d_woffs, woffs);
   upload(c, d_sec, sec_of);
   if (tot_w > 0) work.reset(c, sizeof(double) * tot_w);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    B2_CUDA(cudaEventCreate(&e0));
+    B2_CUDA(cudaEventCreate(&e1));
+    B2_CUDA(cudaEventRecord(e0, c->stream));
+  }
   b2k::launch_jacobi(ns, d_dims.as<int>(), d_offs.as<int64_t>(), d_eoffs.as<int64_t>(),
                      rho.as<double>(), evals.as<double>(), evecs.as<double>(), work.as<double>(),
-                     d_woffs.as<int64_t>(), max_dim, c->stream);
+                     d_woffs.as<int64_t>(), max_dim, c->stream, true,
+                     c->prof ? c->d_eig_flops : nullptr);
+  if (c->prof) {
+    B2_CUDA(cudaEventRecord(e1, c->stream));
+    c->eig_events.push_back({e0, e1});
+  }
   B2_CUDA(cudaGetLastError());
   b2k::launch_select(int(tot_e), evals.as<double>(), d_sec.as<int>(), ns, M, cutoff,
                      d_kept.as<int>(), d_w.as<double>(), c->stream);

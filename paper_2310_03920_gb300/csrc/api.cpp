@@ -84,6 +84,7 @@ void b2_destroy(b2_ctx ctx) {
   cudaStreamSynchronize(ctx->c.stream);
   ctx->c.prof_clear();
   if (ctx->c.d_status) ctx->c.raw_free(ctx->c.d_status);
+  if (ctx->c.d_eig_flops) ctx->c.raw_free(ctx->c.d_eig_flops);
   delete ctx;
 }
 
@@ -380,6 +381,9 @@ int b2_profile(b2_ctx ctx, int enable) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx, B2_EINVAL, "null context");
     B2_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    ensure_device(ctx);
+    if (enable && !ctx->c.d_eig_flops)
+      ctx->c.d_eig_flops = static_cast<double*>(ctx->c.raw_alloc(256));
     ctx->c.prof_clear();
     ctx->c.prof = enable != 0;
     ctx->c.launch_base = b2k::launch_count();
@@ -400,6 +404,17 @@ int b2_profile_read(b2_ctx ctx, b2_profile_data* out) {
     out->heff_launches = int64_t(ctx->c.prof_events.size());
     out->heff_ms = ms;
     out->heff_flops = ctx->c.prof_flops;
+    double ems = 0, ef = 0;
+    for (auto& e : ctx->c.eig_events) {
+      float t = 0;
+      B2_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+      ems += t;
+    }
+    if (ctx->c.d_eig_flops)
+      B2_CUDA(cudaMemcpy(&ef, ctx->c.d_eig_flops, sizeof(double), cudaMemcpyDeviceToHost));
+    out->eig_launches = int64_t(ctx->c.eig_events.size());
+    out->eig_ms = ems;
+    out->eig_flops = ef;
   });
 }
 

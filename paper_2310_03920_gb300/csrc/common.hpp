@@ -58,6 +58,9 @@ struct Ctx {
   long long launch_base = 0;
   double prof_flops = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  // ... and around the truncation eigensolver launches, with its applied-rotation flops
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eig_events;
+  double* d_eig_flops = nullptr;   // device counter (allocated by b2_profile)
   void* raw_alloc(size_t bytes);
   void raw_free(void* p);
   // device status word of bounded waits: allocated and zeroed on first use
@@ -65,12 +68,15 @@ struct Ctx {
   // read (synchronising the stream) and clear the status word; nonzero = a wait ran out
   int take_status();
   void prof_clear() {
-    for (auto& e : prof_events) {
-      cudaEventDestroy(e.first);
-      cudaEventDestroy(e.second);
+    for (auto* v : {&prof_events, &eig_events}) {
+      for (auto& e : *v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+      v->clear();
     }
-    prof_events.clear();
     prof_flops = 0;
+    if (d_eig_flops) cudaMemsetAsync(d_eig_flops, 0, sizeof(double), stream);
   }
 };
 

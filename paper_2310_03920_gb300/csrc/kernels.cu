@@ -307,6 +307,9 @@ constexpr int kJacobiSmemA = 160;
 // matrices, whose smallest eigenvalues are rounding noise, stop after 10-15 sweeps instead
 // of chasing that noise up to kMaxSweeps.
 constexpr double kJacobiAbsTol = 1e-15;
+// Algorithmic flops of one applied rotation of an m x m problem (textbook count: the two
+// rows and two columns of A, 12 m, and two columns of V, 6 m), for the profiling counter.
+constexpr double kJacobiRotFlops = 18.0;
 constexpr int kMaxSweeps = 60;
 constexpr int kJacobiThreads = 512;
 
@@ -386,9 +389,10 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
                                                            double* evals, double* evecs,
                                                            double* work,
                                                            const int64_t* __restrict__ woffs,
-                                                           int max_m) {
+                                                           int max_m, double* flop_counter) {
   extern __shared__ double smem[];
   __shared__ int nrot;
+  long long rot_total = 0;   // thread 0: rotations applied
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int m = dims[b];
   if (m > max_m) return;   // left to k_jacobi_cluster
@@ -498,9 +502,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
       for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
       __syncthreads();
     }
+    if (tid == 0) rot_total += nrot;
     if (nrot == 0) break;
     __syncthreads();
   }
+  if (flop_counter && tid == 0) atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
   // descending order, ties by index
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
@@ -537,7 +543,7 @@ __host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     const int* __restrict__ dims, const int64_t* __restrict__ offs,
     const int64_t* __restrict__ eoffs, const double* __restrict__ a, double* evals,
-    double* evecs, double* work, const int64_t* __restrict__ woffs) {
+    double* evecs, double* work, const int64_t* __restrict__ woffs, double* flop_counter) {
   extern __shared__ double smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int C = int(cl.num_blocks());
@@ -557,6 +563,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   int* perm = qi_ + half;
   int* perm2 = perm + mp;
   __shared__ int nrot;
+  long long rot_total = 0;   // thread 0: rotations applied
   const double* src = a + offs[b];
   for (int e = gt; e < m * m; e += gn) {
     A[e] = src[e];
@@ -644,9 +651,12 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
       cluster_barrier(cl);
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
+    if (tid == 0) rot_total += nrot;
     if (nrot == 0) break;
     __syncthreads();
   }
+  if (flop_counter && crank == 0 && tid == 0)
+    atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
   for (int i = gt; i < m; i += gn) {
@@ -663,7 +673,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
 
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster) {
+                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster,
+                   double* flop_counter) {
   if (n_mat <= 0) return;
   const bool cluster = use_cluster && max_dim > kJacobiClusterMin;
   // the largest per-matrix need over every dimension up to max_dim
@@ -681,7 +692,8 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
     }
   }
   k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
-                                                cluster ? kJacobiClusterMin : INT_MAX);
+                                                cluster ? kJacobiClusterMin : INT_MAX,
+                                                flop_counter);
   g_launches += 1;
   if (!cluster) return;
   // 16 CTAs per cluster where the device runs such clusters, else the portable 8
@@ -723,7 +735,8 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
   attr_c[0].val.clusterDim.z = 1;
   cfg.attrs = attr_c;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs);
+  cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs,
+                     flop_counter);
   g_launches += 1;
 }
 
@@ -980,15 +993,31 @@ void launch_ritz(int k, const double* V, const double* W, int64_t ld, const doub
   g_launches += 1;
 }
 
-__global__ void k_scale_inv_sqrt(double* x, int64_t n, const double* norm2) {
-  double f = 1.0 / sqrt(*norm2);
+// x *= |x|^-1 given |x|^2; the factor is formed once per block (FP64 division and square
+// root are long sequences on GB300's FP64 pipe).  With flag: a norm below 1e-14 (a
+// breakdown of the Davidson basis extension) zeroes x and sets *flag = 1.
+__global__ void k_scale_inv_sqrt(double* x, int64_t n, const double* norm2, double* flag) {
+  __shared__ double f;
+  if (threadIdx.x == 0) {
+    const double nn = *norm2;
+    const bool ok = !flag || sqrt(nn) >= 1e-14;
+    f = ok ? 1.0 / sqrt(nn) : 0.0;
+    if (!ok && blockIdx.x == 0) *flag = 1.0;
+  }
+  __syncthreads();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x)
     x[i] *= f;
 }
 
-void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s) {
-  k_scale_inv_sqrt<<<1024, 256, 0, s>>>(x, n, norm2);
+static int vec_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return int(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s,
+                           double* flag) {
+  k_scale_inv_sqrt<<<vec_blocks(n), 256, 0, s>>>(x, n, norm2, flag);
   g_launches += 1;
 }
 

@@ -141,7 +141,8 @@ inline bool jacobi_needs_work(int dim, bool use_cluster = true) {
 }
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true);
+                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true,
+                   double* flop_counter = nullptr);   // += 18 m per applied rotation
 // Global top-M selection over n eigenvalues (sector-major, descending in each sector).
 // sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
 // (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.
@@ -163,8 +164,9 @@ void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, doub
 void launch_ritz(int k, const double* V, const double* W, int64_t ld, const double* small_evecs,
                  int small_ld, const double* theta, const double* diag, double* u, double* hu,
                  double* t, int64_t n, double* partial, double* out, cudaStream_t s);
-// x *= 1 / sqrt(*norm2)
-void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s);
+// x *= 1 / sqrt(*norm2); with flag (device), a norm below 1e-14 zeroes x and sets *flag = 1
+void launch_scale_inv_sqrt(double* x, int64_t n, const double* norm2, cudaStream_t s,
+                           double* flag = nullptr);
 // x = alpha * y
 void launch_axpby(double* x, const double* y, int64_t n, double a, double b, cudaStream_t s);
 // Build the symmetric k x k Rayleigh matrix from the stored overlaps: g[i*k+j] =
