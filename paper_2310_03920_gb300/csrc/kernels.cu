@@ -524,11 +524,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
 
 // The same rotation sequence for one large matrix (dim > kJacobiClusterMin) spread over a
 // cluster of CTAs: GB300's FP64 rate per SM is low, so one SM per large matrix bounds the
-// whole truncation.  A and V^T stay in the global work space (L2 resident); every round,
-// each CTA computes all the round's rotations from A into its own shared memory (identical
-// in every CTA), the cluster synchronises, the CTAs update disjoint 2 x 2 blocks of A and
-// rows of V^T, and the cluster synchronises again.  Each element sees the same operations
-// in the same order as in k_jacobi, so the results are identical.
+// whole truncation.  A and V^T stay in the global work space (L2 resident).  Every round,
+// each CTA computes all the round's rotations from its own copy of the round's pivots
+// (diagonal entries and pair off-diagonals, identical in every CTA), the CTAs update
+// disjoint 2 x 2 blocks of A and rows of V^T, and the thread that writes a pivot element of
+// the NEXT round also writes it into every CTA's pivot copy (double-buffered by round
+// parity); one cluster barrier per round then orders everything (the kernel is bound by
+// these barriers).  Each element sees the same operations in the same order as in
+// k_jacobi, so the results are identical.
 // One cluster per matrix: the grid is n_mat clusters, clusters of small matrices return at
 // once (uniformly, before any cluster barrier).
 // barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
@@ -536,8 +539,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
 __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { cl.sync(); }
 
 __host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
-  const int mp = m + (m & 1), half = mp / 2;
-  return size_t(half) * (2 * sizeof(double) + 2 * sizeof(int)) + size_t(mp) * 2 * sizeof(int);
+  const int mp = m + (m & 1);
+  return size_t(mp) * (4 * sizeof(double) + 5 * sizeof(int));
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
@@ -556,12 +559,19 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   const int mp = m + (m & 1), half = mp / 2;
   double* A = work + woffs[b];
   double* Vt = A + size_t(m) * m;
+  // shared: rotations of the round, and the pivots of the current and the next round
+  // (by parity: diagonal entries snd[par][x], pair off-diagonals sno[par][k]), written into
+  // every CTA of the cluster by the thread that updates the element
   double* cs = smem;
   double* sn = cs + half;
-  int* pi_ = reinterpret_cast<int*>(sn + half);
+  double* snd = sn + half;        // [2][mp]
+  double* sno = snd + 2 * mp;     // [2][half]
+  int* pi_ = reinterpret_cast<int*>(sno + 2 * half);
   int* qi_ = pi_ + half;
   int* perm = qi_ + half;
   int* perm2 = perm + mp;
+  int* partner = perm2 + mp;      // partner of x in the next round's pairing
+  int* pidx = partner + mp;       // index of x's pair in the next round
   __shared__ int nrot;
   long long rot_total = 0;   // thread 0: rotations applied
   const double* src = a + offs[b];
@@ -573,23 +583,40 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   __shared__ double red[kJacobiThreads / 32];
   const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);   // same in every CTA
   cluster_barrier(cl);
+  // pivots of round 0 (pairs (k, mp-1-k)) from the now complete A, in every CTA
+  for (int x = tid; x < m; x += nt) snd[x] = A[x * m + x];
+  for (int k = tid; k < half; k += nt) {
+    const int p = k, q = mp - 1 - k;
+    sno[k] = q < m ? A[p * m + q] : 0.0;
+  }
+  // element (x, y) of the updated A, v, into the next round's pivots of every CTA
+  auto emit = [&](int np, int x, int y, double v) {
+    double* dst = nullptr;
+    if (x == y)
+      dst = snd + np * mp + x;
+    else if (partner[x] == y)
+      dst = sno + np * half + pidx[x];
+    if (!dst) return;
+    for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(dst, rk) = v;
+  };
+  auto is_pivot = [&](int x, int y) { return x == y || partner[x] == y; };
   const int nblk = half * (half + 1) / 2;
+  int par = 0;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
     for (int round = 0; round < mp - 1; ++round) {
-      // every CTA computes all rotations of the round from the same (global) A: the same
-      // values in every CTA, no exchange between them
+      // rotations of the round from the local pivot copy (same values in every CTA)
       for (int i = tid; i < half; i += nt) {
         int p = perm[i], q = perm[mp - 1 - i];
         if (p > q) { int x = p; p = q; q = x; }
         double c = 1.0, s = 0.0;
         bool rot = false;
         if (q < m) {
-          double apq = A[p * m + q];
+          const double apq = sno[par * half + i];
           if (fabs(apq) > tol) {
-            double app = A[p * m + p], aqq = A[q * m + q];
-            double g = 100.0 * fabs(apq);
+            const double app = snd[par * mp + p], aqq = snd[par * mp + q];
+            const double g = 100.0 * fabs(apq);
             if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
               jacobi_rotation(app, aqq, apq, c, s);
               rot = true;
@@ -602,15 +629,31 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
         qi_[i] = (q < m) ? q : -1;
         if (rot) atomicAdd(&nrot, 1);
       }
-      // every CTA has read the pivots of this round before any CTA updates A
-      cluster_barrier(cl);
+      for (int i = tid; i < mp; i += nt)
+        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
       __syncthreads();
+      for (int k = tid; k < half; k += nt) {
+        const int x = perm2[k], y = perm2[mp - 1 - k];
+        partner[x] = y;
+        partner[y] = x;
+        pidx[x] = k;
+        pidx[y] = k;
+      }
+      __syncthreads();
+      const int np = par ^ 1;
       for (int e = gt; e < nblk; e += gn) {
         int i, j;
         unrank_upper(e, half, i, j);
         const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-        if (si == 0.0 && sj == 0.0) continue;   // identity on this block: nothing changes
         const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
+        if (si == 0.0 && sj == 0.0) {   // identity on this block: only pass on its pivots
+          if (is_pivot(p, r)) emit(np, p, r, A[p * m + r]);
+          if (u >= 0 && is_pivot(p, u)) emit(np, p, u, A[p * m + u]);
+          if (q >= 0 && is_pivot(q, r)) emit(np, q, r, A[q * m + r]);
+          if (q >= 0 && u >= 0 && i != j && is_pivot(q, u)) emit(np, q, u, A[q * m + u]);
+          if (i == j && q >= 0) emit(np, q, q, A[q * m + q]);
+          continue;
+        }
         if (q >= 0 && u >= 0) {
           double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
           double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
@@ -622,16 +665,24 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
           if (i != j) {
             A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
           }
+          emit(np, p, r, n11);
+          emit(np, p, u, n12);
+          if (i != j) emit(np, q, r, n21);   // (q, p) of a diagonal block is (p, q)
+          emit(np, q, u, n22);
         } else if (q >= 0) {
           double ap = A[p * m + r], aq = A[q * m + r];
-          double np = ci * ap - si * aq, nq = si * ap + ci * aq;
-          A[p * m + r] = np; A[q * m + r] = nq;
-          if (i != j) { A[r * m + p] = np; A[r * m + q] = nq; }
+          double np_ = ci * ap - si * aq, nq = si * ap + ci * aq;
+          A[p * m + r] = np_; A[q * m + r] = nq;
+          if (i != j) { A[r * m + p] = np_; A[r * m + q] = nq; }
+          emit(np, p, r, np_);
+          emit(np, q, r, nq);
         } else if (u >= 0) {
           double ar = A[p * m + r], au = A[p * m + u];
           double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
           A[p * m + r] = nr; A[p * m + u] = nu;
           if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
+          emit(np, p, r, nr);
+          emit(np, p, u, nu);
         }
       }
       for (int i = gt >> 5; i < half; i += gn >> 5) {
@@ -644,11 +695,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
           Vt[q * m + k] = s * vp + c * vq;
         }
       }
-      for (int i = tid; i < mp; i += nt)
-        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
-      __syncthreads();
       for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
+      // one barrier per round: the next round reads only its own pivot copy, complete once
+      // every CTA has passed this barrier, before any CTA updates A again
       cluster_barrier(cl);
+      par = np;
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
     if (tid == 0) rot_total += nrot;
@@ -700,6 +751,8 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
   static std::once_flag once;
   static int csize = 8;
   std::call_once(once, [] {
+    cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(jacobi_cluster_smem_bytes(1024)));
     if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
         cudaSuccess) {
       cudaGetLastError();

@@ -116,13 +116,15 @@ struct GemmGroupTc {
   int tile0;
 };
 void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
-                            cudaStream_t s);
+                            cudaStream_t s, bool narrow = false);
 // Split-precision (bf16 hi/lo, three products, FP32 accumulation in TMEM) version of
 // launch_gemm on the tcgen05 tensor cores; tiles are kTcTile x kTcTile.  A bounded wait that
 // runs out writes 1 to *status.
 constexpr int kTcTile = 128;
+// narrow: every tile has at most 64 output columns (smaller shared memory and TMEM
+// footprint, more CTAs per SM).
 void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                    const BufTable& bt, int* status, cudaStream_t s);
+                    const BufTable& bt, int* status, cudaStream_t s, bool narrow = false);
 void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
                  const BufTable& bt, cudaStream_t s);
 void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
