@@ -314,10 +314,12 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     B2_CUDA(cudaEventCreate(&e1));
     B2_CUDA(cudaEventRecord(e0, c->stream));
   }
+  c->side_init();
+  const b2k::JacobiSide side{c->side, c->side_fork, c->side_join};
   b2k::launch_jacobi(ns, d_dims.as<int>(), d_offs.as<int64_t>(), d_eoffs.as<int64_t>(),
                      rho.as<double>(), evals.as<double>(), evecs.as<double>(), work.as<double>(),
                      d_woffs.as<int64_t>(), max_dim, c->stream, true,
-                     c->prof ? c->d_eig_flops : nullptr);
+                     c->prof ? c->d_eig_flops : nullptr, &side);
   if (c->prof) {
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->eig_events.push_back({e0, e1});

@@ -85,6 +85,7 @@ void b2_destroy(b2_ctx ctx) {
   ctx->c.prof_clear();
   if (ctx->c.d_status) ctx->c.raw_free(ctx->c.d_status);
   if (ctx->c.d_eig_flops) ctx->c.raw_free(ctx->c.d_eig_flops);
+  ctx->c.side_destroy();
   delete ctx;
 }
 

@@ -53,6 +53,22 @@ struct Ctx {
   void* user = nullptr;
   std::string last_error;
   int* d_status = nullptr;   // device status word for bounded waits (0 = ok)
+  // side stream and fork/join events (created on first use) for concurrent kernels
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  void side_init() {
+    if (side) return;
+    B2_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    B2_CUDA(cudaEventCreateWithFlags(&side_fork, cudaEventDisableTiming));
+    B2_CUDA(cudaEventCreateWithFlags(&side_join, cudaEventDisableTiming));
+  }
+  void side_destroy() {
+    if (side) cudaStreamDestroy(side);
+    if (side_fork) cudaEventDestroy(side_fork);
+    if (side_join) cudaEventDestroy(side_join);
+    side = nullptr;
+    side_fork = side_join = nullptr;
+  }
   // benchmark profiling (b2_profile): events around H_eff kernel launches
   bool prof = false;
   long long launch_base = 0;

@@ -69,7 +69,6 @@ void GemmProgram::finalize(Ctx* c, bool with_tc) {
   tasks.clear();
   reds.clear();
   tiles_tc.clear();
-  tiles_tc_narrow.clear();
   std::vector<double> tcost;   // per term
   double total = 0;
   for (size_t i = 0; i < outs.size(); ++i) {
@@ -122,9 +121,7 @@ void GemmProgram::finalize(Ctx* c, bool with_tc) {
       }
     if (with_tc)
       for (int r = 0; r < o.M; r += b2k::kTcTile)
-        for (int cc = 0; cc < o.N; cc += b2k::kTcTile)
-          (std::min(b2k::kTcTile, o.N - cc) <= 64 ? tiles_tc_narrow : tiles_tc)
-              .push_back({int(i), r, cc});
+        for (int cc = 0; cc < o.N; cc += b2k::kTcTile) tiles_tc.push_back({int(i), r, cc});
   }
   // most expensive items first (they are dispatched first)
   std::vector<double> cost(tasks.size());
@@ -147,10 +144,7 @@ void GemmProgram::finalize(Ctx* c, bool with_tc) {
   upload(c, d_tasks, tasks);
   upload(c, d_reds, reds);
   if (slots > 0) d_partial.reset(c, sizeof(double) * size_t(slots) * b2k::kTile * b2k::kTile);
-  if (with_tc) {
-    upload(c, d_tiles_tc, tiles_tc);
-    upload(c, d_tiles_tc_narrow, tiles_tc_narrow);
-  }
+  if (with_tc) upload(c, d_tiles_tc, tiles_tc);
 }
 
 void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
@@ -161,14 +155,10 @@ void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
 }
 
 void GemmProgram::launch_tc(Ctx* c, const BufTable& bt) const {
-  B2_REQUIRE((d_tiles_tc.ptr != nullptr || tiles_tc.empty()) &&
-                 (d_tiles_tc_narrow.ptr != nullptr || tiles_tc_narrow.empty()),
-             B2_EINVAL, "internal: program finalized without tensor-core tiles");
+  B2_REQUIRE(d_tiles_tc.ptr != nullptr || tiles_tc.empty(), B2_EINVAL,
+             "internal: program finalized without tensor-core tiles");
   b2k::launch_gemm_tc(d_tiles_tc.as<b2k::GemmTile>(), int(tiles_tc.size()), d_outs.as<b2k::GemmOut>(),
-                      d_terms.as<GemmTerm>(), bt, c->status(), c->stream, false);
-  b2k::launch_gemm_tc(d_tiles_tc_narrow.as<b2k::GemmTile>(), int(tiles_tc_narrow.size()),
-                      d_outs.as<b2k::GemmOut>(), d_terms.as<GemmTerm>(), bt, c->status(),
-                      c->stream, true);
+                      d_terms.as<GemmTerm>(), bt, c->status(), c->stream);
   B2_CUDA(cudaGetLastError());
 }
 
@@ -704,8 +694,8 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
                         const double* const* psis, double* const* outs, b2_prec prec,
                         double* flops) {
   std::vector<b2k::GemmGroup> groups;
-  std::vector<b2k::GemmGroupTc> groups_tc, groups_tcn;
-  int items = 0, reds = 0, tiles = 0, tiles_n = 0;
+  std::vector<b2k::GemmGroupTc> groups_tc;
+  int items = 0, reds = 0, tiles = 0;
   double fl = 0;
   for (int i = 0; i < n; ++i) {
     b2_env_s* env = envs[i];
@@ -735,14 +725,10 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
       groups_tc.push_back({wp.heff.d_tiles_tc.as<b2k::GemmTile>(), wp.heff.d_outs.as<b2k::GemmOut>(),
                            wp.heff.d_terms.as<GemmTerm>(), bt, tiles});
       tiles += int(wp.heff.tiles_tc.size());
-      groups_tcn.push_back({wp.heff.d_tiles_tc_narrow.as<b2k::GemmTile>(),
-                            wp.heff.d_outs.as<b2k::GemmOut>(), wp.heff.d_terms.as<GemmTerm>(), bt,
-                            tiles_n});
-      tiles_n += int(wp.heff.tiles_tc_narrow.size());
     }
     fl += wp.heff.flops;
   }
-  DevBuf d_groups, d_groups_n;
+  DevBuf d_groups;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->prof) {
     B2_CUDA(cudaEventCreate(&e0));
@@ -755,12 +741,9 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
                              c->stream);
   } else {
     upload(c, d_groups, groups_tc);
-    upload(c, d_groups_n, groups_tcn);
     if (e0) B2_CUDA(cudaEventRecord(e0, c->stream));
     b2k::launch_gemm_tc_grouped(d_groups.as<b2k::GemmGroupTc>(), int(groups_tc.size()), tiles,
-                                c->status(), c->stream, false);
-    b2k::launch_gemm_tc_grouped(d_groups_n.as<b2k::GemmGroupTc>(), int(groups_tcn.size()),
-                                tiles_n, c->status(), c->stream, true);
+                                c->status(), c->stream);
   }
   B2_CUDA(cudaGetLastError());
   if (e0) {

@@ -15,9 +15,8 @@ struct GemmProgram {
   std::vector<b2k::GemmTerm> terms;
   std::vector<b2k::GemmTask> tasks;              // FP64 work items (32x32 tiles, term ranges)
   std::vector<b2k::GemmReduce> reds;             // fixed-order sums of split tiles
-  std::vector<b2k::GemmTile> tiles_tc;           // 128x128 tensor-core tiles (> 64 columns)
-  std::vector<b2k::GemmTile> tiles_tc_narrow;    // tensor-core tiles of <= 64 columns
-  DevBuf d_terms, d_outs, d_tasks, d_reds, d_partial, d_tiles_tc, d_tiles_tc_narrow;
+  std::vector<b2k::GemmTile> tiles_tc;           // 128x128 tensor-core tiles
+  DevBuf d_terms, d_outs, d_tasks, d_reds, d_partial, d_tiles_tc;
   double flops = 0;
   int add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate);
   void add_term(int out, const b2k::GemmTerm& t);

@@ -725,9 +725,17 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster,
-                   double* flop_counter) {
+                   double* flop_counter, const JacobiSide* side) {
   if (n_mat <= 0) return;
   const bool cluster = use_cluster && max_dim > kJacobiClusterMin;
+  // With a side stream, the one-CTA kernel (small matrices) runs there, concurrently with
+  // the cluster kernel (large ones) on s: they touch disjoint matrices and outputs.
+  cudaStream_t s_small = s;
+  if (cluster && side && side->stream) {
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->stream, side->fork, 0);
+    s_small = side->stream;
+  }
   // the largest per-matrix need over every dimension up to max_dim
   size_t smem = 0;
   const int single_max = cluster ? kJacobiClusterMin : max_dim;
@@ -742,9 +750,9 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
       attr = smem;
     }
   }
-  k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
-                                                cluster ? kJacobiClusterMin : INT_MAX,
-                                                flop_counter);
+  k_jacobi<<<n_mat, kJacobiThreads, smem, s_small>>>(dims, offs, eoffs, a, evals, evecs, work,
+                                                      woffs, cluster ? kJacobiClusterMin : INT_MAX,
+                                                      flop_counter);
   g_launches += 1;
   if (!cluster) return;
   // 16 CTAs per cluster where the device runs such clusters, else the portable 8
@@ -791,6 +799,10 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
   cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs,
                      flop_counter);
   g_launches += 1;
+  if (s_small != s) {   // join: s waits for the one-CTA kernel
+    cudaEventRecord(side->join, s_small);
+    cudaStreamWaitEvent(s, side->join, 0);
+  }
 }
 
 // ======================================================================= selection

@@ -116,15 +116,13 @@ struct GemmGroupTc {
   int tile0;
 };
 void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
-                            cudaStream_t s, bool narrow = false);
+                            cudaStream_t s);
 // Split-precision (bf16 hi/lo, three products, FP32 accumulation in TMEM) version of
 // launch_gemm on the tcgen05 tensor cores; tiles are kTcTile x kTcTile.  A bounded wait that
 // runs out writes 1 to *status.
 constexpr int kTcTile = 128;
-// narrow: every tile has at most 64 output columns (smaller shared memory and TMEM
-// footprint, more CTAs per SM).
 void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                    const BufTable& bt, int* status, cudaStream_t s, bool narrow = false);
+                    const BufTable& bt, int* status, cudaStream_t s);
 void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
                  const BufTable& bt, cudaStream_t s);
 void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
@@ -138,13 +136,20 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 // one CTA; the others by one CTA each.
 constexpr int kJacobiSmemAV = 112;
 constexpr int kJacobiClusterMin = 64;
+// Optional second stream (with a fork and a join event) on which the one-CTA kernel runs
+// concurrently with the cluster kernel.
+struct JacobiSide {
+  cudaStream_t stream;
+  cudaEvent_t fork, join;
+};
 inline bool jacobi_needs_work(int dim, bool use_cluster = true) {
   return dim > (use_cluster ? kJacobiClusterMin : kJacobiSmemAV);
 }
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true,
-                   double* flop_counter = nullptr);   // += 18 m per applied rotation
+                   double* flop_counter = nullptr,   // += 18 m per applied rotation
+                   const JacobiSide* side = nullptr);
 // Global top-M selection over n eigenvalues (sector-major, descending in each sector).
 // sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
 // (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.

@@ -140,21 +140,16 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
 
 }  // namespace
 
-// kNarrow: every tile of the launch has at most 64 output columns, so the B operand needs
-// 64 rows (half the shared memory) and the accumulator 64 TMEM columns (128 allocated
-// instead of 256): four CTAs fit on an SM instead of two (the kernel is latency-bound).
-template <bool kNarrow>
 __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut* __restrict__ outs,
                                              const GemmTerm* __restrict__ terms, const BufTable& bt,
                                              int* status) {
-  constexpr uint32_t kAlloc = kNarrow ? 128 : kTmemCols;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* a_hi = base;                       // A operand (128 x 64)
   unsigned char* a_lo = base + kTileBytes;
-  unsigned char* b_hi = base + 2 * kTileBytes;      // B operand (<= 128, or 64, x 64)
-  unsigned char* b_lo = b_hi + (kNarrow ? kTileBytes / 2 : kTileBytes);
+  unsigned char* b_hi = base + 2 * kTileBytes;      // B operand (<= 128 x 64)
+  unsigned char* b_lo = base + 3 * kTileBytes;
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
 
@@ -167,7 +162,7 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(kAlloc));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -178,7 +173,7 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t tmem_t = tmem, tmem_acc = tmem + (kNarrow ? 64 : 128);
+  const uint32_t tmem_t = tmem, tmem_acc = tmem + 128;
   const uint32_t lane_off = uint32_t(warp * 32) << 16;
 
   // rows of the A operand beyond the output block stay zero for every term
@@ -299,20 +294,18 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAlloc));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <bool kNarrow>
 __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles,
                                                  const GemmOut* __restrict__ outs,
                                                  const GemmTerm* __restrict__ terms, BufTable bt,
                                                  int* status) {
-  gemm_tc_item<kNarrow>(tiles[blockIdx.x], outs, terms, bt, status);
+  gemm_tc_item(tiles[blockIdx.x], outs, terms, bt, status);
 }
 
 // Grouped launch over several problems: CTA b takes tile b - tile0 of the group g with
 // tile0(g) <= b < tile0(g + 1).
-template <bool kNarrow>
 __global__ void __launch_bounds__(128) k_gemm_tc_grouped(const GemmGroupTc* __restrict__ groups,
                                                          int n_groups, int* status) {
   int lo = 0, hi = n_groups - 1;
@@ -323,42 +316,31 @@ __global__ void __launch_bounds__(128) k_gemm_tc_grouped(const GemmGroupTc* __re
   }
   const GemmGroupTc& G = groups[lo];
   const BufTable bt = G.bt;
-  gemm_tc_item<kNarrow>(G.tiles[b - G.tile0], G.outs, G.terms, bt, status);
+  gemm_tc_item(G.tiles[b - G.tile0], G.outs, G.terms, bt, status);
 }
 
-size_t gemm_tc_smem(bool narrow) { return size_t(narrow ? 3 : 4) * kTileBytes + 1024; }
+size_t gemm_tc_smem() { return size_t(4) * kTileBytes + 1024; }
 
 void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                    const BufTable& bt, int* status, cudaStream_t s, bool narrow) {
+                    const BufTable& bt, int* status, cudaStream_t s) {
   if (n_tiles <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(gemm_tc_smem(false)));
-    cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(gemm_tc_smem(true)));
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
   });
-  if (narrow)
-    k_gemm_tc<true><<<n_tiles, 128, gemm_tc_smem(true), s>>>(tiles, outs, terms, bt, status);
-  else
-    k_gemm_tc<false><<<n_tiles, 128, gemm_tc_smem(false), s>>>(tiles, outs, terms, bt, status);
+  k_gemm_tc<<<n_tiles, 128, gemm_tc_smem(), s>>>(tiles, outs, terms, bt, status);
   count_launches(1);
 }
 
 void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
-                            cudaStream_t s, bool narrow) {
+                            cudaStream_t s) {
   if (n_groups <= 0 || n_tiles <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_gemm_tc_grouped<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(gemm_tc_smem(false)));
-    cudaFuncSetAttribute(k_gemm_tc_grouped<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(gemm_tc_smem(true)));
+    cudaFuncSetAttribute(k_gemm_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(gemm_tc_smem()));
   });
-  if (narrow)
-    k_gemm_tc_grouped<true><<<n_tiles, 128, gemm_tc_smem(true), s>>>(groups, n_groups, status);
-  else
-    k_gemm_tc_grouped<false><<<n_tiles, 128, gemm_tc_smem(false), s>>>(groups, n_groups, status);
+  k_gemm_tc_grouped<<<n_tiles, 128, gemm_tc_smem(), s>>>(groups, n_groups, status);
   count_launches(1);
 }
 
