@@ -62,6 +62,20 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ranks(t_tot, flops, device):
+    """Whole-job figures of N independent replicas: time = max over ranks, flops = sum over
+    ranks (one process per GPU; identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_tot, flops
+    t = torch.tensor([t_tot], dtype=torch.float64, device=device)
+    f = torch.tensor([flops], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(f[0])
+
+
 def dist_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -540,14 +554,7 @@ def main():
     b2.b2_profile(ctx, False)
     t_step = sum(step_ms) / len(step_ms)
     t_tot = sum(step_ms) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t_tot, flops], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_tot, flops_all = float(mx[0]), float(tt[1])
-    else:
-        flops_all = flops
+    t_tot, flops_all = aggregate_ranks(t_tot, flops, "cuda")
     value = flops_all / t_tot / 1e12
 
     # e2e through the public API from host buffers: import, env, one sweep, export
