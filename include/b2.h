@@ -241,9 +241,10 @@ int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts*
 
 /* ------------------------------------------------------------------ batched eigensolver
  * Eigen-decomposition of n_mat real symmetric matrices by cyclic Jacobi rotations in
- * FP64 (one thread block per matrix of dim <= 64, a cluster of 16 thread blocks -- 8 where
- * the device cannot run 16 -- per larger matrix, same results): the density-matrix step of
- * the truncation.  Rotations stop once
+ * FP64: the density-matrix step of the truncation.  Each matrix gets one thread block or a
+ * cluster of 2 to 16 (8 where the device cannot run 16), sized on the host from the dims so
+ * that the batch spreads over the SMs with the largest matrices on the largest clusters;
+ * every size gives the same results (bitwise).  Rotations stop once
  * every off-diagonal element is below 1e-15 times the largest input element (or negligible
  * next to its diagonal entries): eigenvalues and eigenvectors are accurate to about that
  * fraction of the largest element, as from a backward-stable solver.
@@ -296,17 +297,20 @@ int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every
- * launch of the H_eff contraction kernel and of the truncation eigensolver is bracketed by
- * CUDA events on the context stream, and every kernel launch of the library is counted.
+ * launch of the H_eff contraction kernel, of the truncation eigensolver and of the Davidson
+ * Rayleigh-Ritz eigensolver is bracketed by CUDA events on the context stream, and every
+ * kernel launch of the library is counted.
  * b2_profile(ctx, 1) also resets the counters. */
 typedef struct {
   int64_t launches;        /* kernel launches of the library since the reset */
   int64_t heff_launches;   /* H_eff contraction kernel launches timed */
   double heff_ms;          /* their summed device time */
   double heff_flops;       /* their summed algorithmic flops */
-  int64_t eig_launches;    /* truncation eigensolver calls timed (one or two kernels each) */
+  int64_t eig_launches;    /* truncation eigensolver calls timed (a kernel per cluster size) */
   double eig_ms;           /* their summed device time */
   double eig_flops;        /* 18 m flops per applied Jacobi rotation of an m x m block */
+  int64_t rr_launches;     /* Davidson Rayleigh-Ritz eigensolves timed (k x k, one CTA) */
+  double rr_ms;            /* their summed device time */
 } b2_profile_data;
 int b2_profile(b2_ctx ctx, int enable);
 int b2_profile_read(b2_ctx ctx, b2_profile_data* out);

@@ -46,7 +46,8 @@ class SweepResult(ctypes.Structure):
 
 class ProfileData(ctypes.Structure):
     _fields_ = [("launches", _i64), ("heff_launches", _i64), ("heff_ms", _d), ("heff_flops", _d),
-                ("eig_launches", _i64), ("eig_ms", _d), ("eig_flops", _d)]
+                ("eig_launches", _i64), ("eig_ms", _d), ("eig_flops", _d),
+                ("rr_launches", _i64), ("rr_ms", _d)]
 
 
 _sig = {

@@ -44,6 +44,40 @@ struct Tracer {
   }
 };
 
+void eigh_batched(Ctx* c, const std::vector<int>& dims, const std::vector<int64_t>& offs,
+                  const std::vector<int64_t>& eoffs, const double* a, double* evals,
+                  double* evecs, double* flop_counter) {
+  const int n = int(dims.size());
+  if (n == 0) return;
+  const b2k::JacobiPlan plan = b2k::plan_jacobi(dims);
+  std::vector<int64_t> woffs(n, 0);
+  int64_t tot_w = 0;
+  for (int j = 0; j < n; ++j)
+    if (b2k::jacobi_needs_work(dims[j], plan.csize[j])) {
+      woffs[j] = tot_w;
+      tot_w += 2 * int64_t(dims[j]) * dims[j];
+    }
+  DevBuf d_dims, d_offs, d_eoffs, d_woffs, d_ids, work;
+  upload(c, d_dims, dims);
+  upload(c, d_offs, offs);
+  upload(c, d_eoffs, eoffs);
+  upload(c, d_woffs, woffs);
+  upload(c, d_ids, plan.ids);
+  if (tot_w > 0) work.reset(c, sizeof(double) * tot_w);
+  c->side_init();
+  static_assert(Ctx::kSides >= b2k::kJacobiClasses - 1, "one side stream per extra class");
+  b2k::JacobiStreams side{};
+  for (int k = 0; k < b2k::kJacobiClasses - 1; ++k) {
+    side.stream[k] = c->side[k];
+    side.join[k] = c->side_join[k];
+  }
+  side.fork = c->side_fork;
+  b2k::launch_jacobi_plan(plan, d_ids.as<int>(), d_dims.as<int>(), d_offs.as<int64_t>(),
+                          d_eoffs.as<int64_t>(), a, evals, evecs, work.as<double>(),
+                          d_woffs.as<int64_t>(), c->stream, &side, flop_counter);
+  B2_CUDA(cudaGetLastError());
+}
+
 // ------------------------------------------------------------ two-site contraction
 // out(jl, s1, s2) = sum_jm X(jl, s1 -> jm) Y(jm, s2 -> jr) for a psi layout on bonds (a, c);
 // X on bonds (a, b), Y on bonds (b, c).
@@ -138,9 +172,19 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
   double brk = 0;
   bool stop_after_ritz = false;
   for (;;) {
+    cudaEvent_t r0 = nullptr, r1 = nullptr;
+    if (c->prof) {
+      B2_CUDA(cudaEventCreate(&r0));
+      B2_CUDA(cudaEventCreate(&r1));
+      B2_CUDA(cudaEventRecord(r0, c->stream));
+    }
     b2k::launch_symmetrize(k, VW, kmax, G, c->stream);
     b2k::launch_jacobi(1, d_dims.as<int>() + k, d_offs.as<int64_t>(), d_offs.as<int64_t>(), G,
                        evals, evecs, nullptr, d_offs.as<int64_t>(), k, c->stream);
+    if (c->prof) {
+      B2_CUDA(cudaEventRecord(r1, c->stream));
+      c->rr_events.push_back({r0, r1});
+    }
     // lowest Ritz pair: last of the descending eigenvalues, column k-1
     b2k::launch_ritz(k, Vp, Wp, n, evecs + (k - 1), k, evals + (k - 1), diag.as<double>(),
                      u.as<double>(), hu.as<double>(), t.as<double>(), n, part, scal, c->stream);
@@ -274,8 +318,8 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
                                        double* discarded) {
   int ns = int(secs.size());
   std::vector<int> dims(ns), sec_of;
-  std::vector<int64_t> offs(ns), eoffs(ns), woffs(ns, 0);
-  int64_t tot_e = 0, tot_w = 0;
+  std::vector<int64_t> offs(ns), eoffs(ns);
+  int64_t tot_e = 0;
   int max_dim = 0;
   for (int j = 0; j < ns; ++j) {
     dims[j] = secs[j].dim;
@@ -283,10 +327,6 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     eoffs[j] = secs[j].eoff;
     tot_e += dims[j];
     max_dim = std::max(max_dim, dims[j]);
-    if (b2k::jacobi_needs_work(dims[j])) {
-      woffs[j] = tot_w;
-      tot_w += 2 * int64_t(dims[j]) * dims[j];
-    }
     for (int t = 0; t < dims[j]; ++t) sec_of.push_back(j);
   }
   if (std::getenv("B2_TRACE_TIME")) {
@@ -300,31 +340,20 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
   }
   B2_REQUIRE(max_dim <= 1024, B2_EUNSUPPORTED, "density-matrix sector larger than 1024");
   B2_REQUIRE(tot_e <= b2k::kSelectMax, B2_EUNSUPPORTED, "too many density-matrix eigenvalues");
-  DevBuf d_dims, d_offs, d_eoffs, d_woffs, d_sec, work, d_kept(c, sizeof(int) * ns + 16),
-      d_w(c, 2 * sizeof(double));
-  upload(c, d_dims, dims);
-  upload(c, d_offs, offs);
-  upload(c, d_eoffs, eoffs);
-  upload(c, d_woffs, woffs);
+  DevBuf d_sec, d_kept(c, sizeof(int) * ns + 16), d_w(c, 2 * sizeof(double));
   upload(c, d_sec, sec_of);
-  if (tot_w > 0) work.reset(c, sizeof(double) * tot_w);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->prof) {
     B2_CUDA(cudaEventCreate(&e0));
     B2_CUDA(cudaEventCreate(&e1));
     B2_CUDA(cudaEventRecord(e0, c->stream));
   }
-  c->side_init();
-  const b2k::JacobiSide side{c->side, c->side_fork, c->side_join};
-  b2k::launch_jacobi(ns, d_dims.as<int>(), d_offs.as<int64_t>(), d_eoffs.as<int64_t>(),
-                     rho.as<double>(), evals.as<double>(), evecs.as<double>(), work.as<double>(),
-                     d_woffs.as<int64_t>(), max_dim, c->stream, true,
-                     c->prof ? c->d_eig_flops : nullptr, &side);
+  eigh_batched(c, dims, offs, eoffs, rho.as<double>(), evals.as<double>(), evecs.as<double>(),
+               c->prof ? c->d_eig_flops : nullptr);
   if (c->prof) {
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->eig_events.push_back({e0, e1});
   }
-  B2_CUDA(cudaGetLastError());
   b2k::launch_select(int(tot_e), evals.as<double>(), d_sec.as<int>(), ns, M, cutoff,
                      d_kept.as<int>(), d_w.as<double>(), c->stream);
   B2_CUDA(cudaGetLastError());

@@ -287,30 +287,16 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
     ensure_device(ctx);
     b2::Ctx* c = &ctx->c;
     std::vector<int> d(dims, dims + n_mat);
-    std::vector<int64_t> offs(n_mat), eoffs(n_mat), woffs(n_mat, 0);
-    int64_t o = 0, e = 0, w = 0;
-    int max_dim = 0;
+    std::vector<int64_t> offs(n_mat), eoffs(n_mat);
+    int64_t o = 0, e = 0;
     for (int i = 0; i < n_mat; ++i) {
       B2_REQUIRE(d[i] >= 1 && d[i] <= 1024, B2_EINVAL, "dims must be in [1, 1024]");
       offs[i] = o;
       eoffs[i] = e;
       o += int64_t(d[i]) * d[i];
       e += d[i];
-      if (b2k::jacobi_needs_work(d[i])) {
-        woffs[i] = w;
-        w += 2 * int64_t(d[i]) * d[i];
-      }
-      max_dim = std::max(max_dim, d[i]);
     }
-    if (n_mat == 0) return;
-    b2::DevBuf dd, doff, deoff, dwoff, work;
-    b2::upload(c, dd, d);
-    b2::upload(c, doff, offs);
-    b2::upload(c, deoff, eoffs);
-    b2::upload(c, dwoff, woffs);
-    if (w > 0) work.reset(c, sizeof(double) * w);
-    b2k::launch_jacobi(n_mat, dd.as<int>(), doff.as<int64_t>(), deoff.as<int64_t>(), a, evals, evecs,
-                       work.as<double>(), dwoff.as<int64_t>(), max_dim, c->stream);
+    b2::eigh_batched(c, d, offs, eoffs, a, evals, evecs);
     B2_CUDA(cudaGetLastError());
     B2_CUDA(cudaStreamSynchronize(c->stream));
   });
@@ -416,6 +402,14 @@ int b2_profile_read(b2_ctx ctx, b2_profile_data* out) {
     out->eig_launches = int64_t(ctx->c.eig_events.size());
     out->eig_ms = ems;
     out->eig_flops = ef;
+    double rms = 0;
+    for (auto& e : ctx->c.rr_events) {
+      float t = 0;
+      B2_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+      rms += t;
+    }
+    out->rr_launches = int64_t(ctx->c.rr_events.size());
+    out->rr_ms = rms;
   });
 }
 

@@ -53,21 +53,31 @@ struct Ctx {
   void* user = nullptr;
   std::string last_error;
   int* d_status = nullptr;   // device status word for bounded waits (0 = ok)
-  // side stream and fork/join events (created on first use) for concurrent kernels
-  cudaStream_t side = nullptr;
-  cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  // side streams and fork/join events (created on first use) for concurrent kernels
+  static constexpr int kSides = 4;
+  cudaStream_t side[kSides] = {};
+  cudaEvent_t side_fork = nullptr;
+  cudaEvent_t side_join[kSides] = {};
   void side_init() {
-    if (side) return;
-    B2_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    if (side_fork) return;
+    // side stream 0 at the device's highest priority (see b2k::JacobiStreams)
+    int lo = 0, hi = 0;
+    B2_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    for (int k = 0; k < kSides; ++k) {
+      B2_CUDA(cudaStreamCreateWithPriority(&side[k], cudaStreamNonBlocking, k == 0 ? hi : lo));
+      B2_CUDA(cudaEventCreateWithFlags(&side_join[k], cudaEventDisableTiming));
+    }
     B2_CUDA(cudaEventCreateWithFlags(&side_fork, cudaEventDisableTiming));
-    B2_CUDA(cudaEventCreateWithFlags(&side_join, cudaEventDisableTiming));
   }
   void side_destroy() {
-    if (side) cudaStreamDestroy(side);
+    for (int k = 0; k < kSides; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (side_join[k]) cudaEventDestroy(side_join[k]);
+      side[k] = nullptr;
+      side_join[k] = nullptr;
+    }
     if (side_fork) cudaEventDestroy(side_fork);
-    if (side_join) cudaEventDestroy(side_join);
-    side = nullptr;
-    side_fork = side_join = nullptr;
+    side_fork = nullptr;
   }
   // benchmark profiling (b2_profile): events around H_eff kernel launches
   bool prof = false;
@@ -77,6 +87,8 @@ struct Ctx {
   // ... and around the truncation eigensolver launches, with its applied-rotation flops
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eig_events;
   double* d_eig_flops = nullptr;   // device counter (allocated by b2_profile)
+  // ... and around the Davidson Rayleigh-Ritz eigensolver (k x k projected matrix)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rr_events;
   void* raw_alloc(size_t bytes);
   void raw_free(void* p);
   // device status word of bounded waits: allocated and zeroed on first use
@@ -84,7 +96,7 @@ struct Ctx {
   // read (synchronising the stream) and clear the status word; nonzero = a wait ran out
   int take_status();
   void prof_clear() {
-    for (auto* v : {&prof_events, &eig_events}) {
+    for (auto* v : {&prof_events, &eig_events, &rr_events}) {
       for (auto& e : *v) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);

@@ -61,26 +61,9 @@ std::unique_ptr<b2_mps_s> copy_mps(Ctx* c, const b2_mps_s* m) {
 void gram_factors(Ctx* c, const std::vector<int>& dims, const std::vector<int64_t>& goff,
                   const std::vector<int64_t>& eoff, DevBuf& G, DevBuf& U, DevBuf& lam, DevBuf& U1,
                   DevBuf& U2) {
-  std::vector<int64_t> woff(dims.size(), 0);
-  int64_t wsize = 0;
-  int max_dim = 0;
-  for (size_t j = 0; j < dims.size(); ++j) {
+  for (size_t j = 0; j < dims.size(); ++j)
     B2_REQUIRE(dims[j] <= 1024, B2_EUNSUPPORTED, "gradient: bond sector larger than 1024 states");
-    max_dim = std::max(max_dim, dims[j]);
-    if (b2k::jacobi_needs_work(dims[j])) {
-      woff[j] = wsize;
-      wsize += 2 * int64_t(dims[j]) * dims[j];
-    }
-  }
-  DevBuf d_dims, d_goff, d_eoff, d_woff, work;
-  upload(c, d_dims, dims);
-  upload(c, d_goff, goff);
-  upload(c, d_eoff, eoff);
-  upload(c, d_woff, woff);
-  if (wsize) work.reset(c, sizeof(double) * wsize);
-  b2k::launch_jacobi(int(dims.size()), d_dims.as<int>(), d_goff.as<int64_t>(), d_eoff.as<int64_t>(),
-                     G.as<double>(), lam.as<double>(), U.as<double>(), work.as<double>(),
-                     d_woff.as<int64_t>(), max_dim, c->stream);
+  eigh_batched(c, dims, goff, eoff, G.as<double>(), lam.as<double>(), U.as<double>());
   // Directions with Gram eigenvalue below kNullGram carry at most sqrt(kNullGram) of the
   // (normalised) state; they are dropped from both factors rather than blown up by lam^-1/2.
   constexpr double kNullGram = 1e-28;

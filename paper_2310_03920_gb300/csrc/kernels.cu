@@ -2,6 +2,7 @@
 // H_eff diagonal, the batched Jacobi eigensolver, truncation selection, block copies and
 // the Davidson vector operations.  All loops over data are bounded by sizes passed in;
 // there are no device-side waits.
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <climits>
@@ -313,16 +314,29 @@ constexpr double kJacobiRotFlops = 18.0;
 constexpr int kMaxSweeps = 60;
 constexpr int kJacobiThreads = 512;
 
-// dynamic shared memory needed by a matrix of dimension m
+// dynamic shared memory needed by a matrix of dimension m: A (dim <= kJacobiSmemA) and
+// V^T (dim <= kJacobiSmemAV), then the round's rotations (c, s, pair rows p, q) and the list
+// of the pairs that rotate
 __host__ __device__ inline size_t jacobi_smem_bytes(int m) {
-  const int mp = m + (m & 1);
-  size_t aux = size_t(mp) * (2 * sizeof(int)) + size_t(mp / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+  const int half = (m + (m & 1)) / 2;
+  size_t aux = size_t(half) * (2 * sizeof(double) + 3 * sizeof(int));
   size_t mat = 0;
   if (m <= kJacobiSmemAV)
     mat = 2 * size_t(m) * m * sizeof(double);
   else if (m <= kJacobiSmemA)
     mat = size_t(m) * m * sizeof(double);
   return mat + aux;
+}
+
+// Round-robin ("tournament") pairing of the cyclic sweep for an even count mp: index 0 stays
+// at position 0 and indices 1..mp-1 move one position on per round, so in round r position
+// i holds jacobi_at(i, r) and index x sits at jacobi_pos(x, r); pair k of the round is
+// (positions k and mp-1-k).  Rounds are taken modulo mp-1 (a sweep has mp-1 rounds).
+__device__ __forceinline__ int jacobi_at(int i, int r, int mp) {
+  return i == 0 ? 0 : 1 + (i - 1 - r + (mp - 1)) % (mp - 1);
+}
+__device__ __forceinline__ int jacobi_pos(int x, int r, int mp) {
+  return x == 0 ? 0 : 1 + (x - 1 + r) % (mp - 1);
 }
 
 // max |src[e]| over e < n, returned to every thread of the block (red: >= 32 doubles)
@@ -341,34 +355,52 @@ __device__ double block_max_abs(const double* __restrict__ src, int n, double* r
 
 // Rotation (c, s) annihilating a_pq of the 2 x 2 pivot [app apq; apq aqq] (the smaller of
 // the two angles, t = tan = s / c the root of apq t^2 + (aqq - app) t - apq = 0 with
-// |t| <= 1).  FP64 division and square root are long dependent chains on GB300's narrow
-// FP64 pipe and sat on the critical path of every round, so t starts from FP32 arithmetic
-// and is refined by two Newton steps in FP64 whose divisor is an FP32 reciprocal of the
-// derivative (each step multiplies the error by ~1e-7), and c = (1 + t^2)^(-1/2) starts
-// from an FP32 reciprocal square root refined by two FP64 Newton steps y(3 - x y^2)/2: the
-// rotation equals the exactly computed one to rounding and is orthogonal to rounding.  The
-// pivot is scaled by a power of two first, so that FP32 neither overflows nor underflows.
+// |t| <= 1).  The kernels scale the matrix by a power of two on entry so that max |a| lies
+// in [0.5, 1): every pivot that rotates (|a_pq| above 1e-15 of that) is then a normal FP32
+// number.  GB300 runs FP64 at about 1.75 operations per clock per SM, and this dependent
+// chain sits on the critical path of every round, so t comes from FP32 arithmetic and is
+// refined by two chord-Newton steps in FP64 that reuse one FP32 reciprocal of the derivative
+// 2 apq t + (aqq - app) (each step multiplies the error by ~1e-7), and c = (1 + t^2)^(-1/2)
+// from an FP32 reciprocal square root refined by two FP64 Newton steps y(3 - x y^2)/2:
+// 16 FP64 operations, and the rotation equals the exactly computed one to rounding and is
+// orthogonal to rounding.
 __device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& c,
                                                 double& s) {
   const double d = aqq - app;
-  const int ex = max(ilogb(fmax(fabs(d), fabs(apq))), -1000);
-  const double ds = scalbn(d, -ex), ps = scalbn(apq, -ex);
-  const float tau = static_cast<float>(ds) / (2.0f * static_cast<float>(ps));
+  const float d32 = static_cast<float>(d), p32 = static_cast<float>(apq);
+  const float tau = d32 / (2.0f * p32);
   const float t32 = fabsf(tau) > 1e18f ? 0.5f / tau
                                         : copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  const double r = 1.0f / fmaf(2.0f * p32, t32, d32);
   double t = t32;
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double f = fma(fma(ps, t, ds), t, -ps);
-    const double r = 1.0f / static_cast<float>(fma(2.0 * ps, t, ds));
-    t = fma(-f, r, t);
-  }
-  const double x = fma(t, t, 1.0);
-  double y = rsqrtf(static_cast<float>(x));
+  for (int it = 0; it < 2; ++it) t = fma(-fma(fma(apq, t, d), t, -apq), r, t);
+  const double hx = 0.5 * fma(t, t, 1.0);
+  double y = rsqrtf(fmaf(t32, t32, 1.0f));
 #pragma unroll
-  for (int it = 0; it < 2; ++it) y = y * fma(-0.5 * x * y, y, 1.5);
+  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
   c = y;
   s = t * y;
+}
+
+// Pivot test of the sweep: rotate unless |a_pq| <= tol (tol_bits: the bit pattern of tol >= 0)
+// or a_pq is negligible next to both diagonal entries (binary exponent at least 61 below
+// each).  Integer operations on the bit patterns, none on the FP64 pipe.
+__device__ __forceinline__ bool jacobi_rotates(double app, double aqq, double apq,
+                                               long long tol_bits) {
+  const long long bp = __double_as_longlong(apq) & 0x7fffffffffffffffLL;
+  if (bp <= tol_bits) return false;
+  const int ep = int(bp >> 52);
+  const int e1 = int((__double_as_longlong(app) >> 52) & 0x7ff);
+  const int e2 = int((__double_as_longlong(aqq) >> 52) & 0x7ff);
+  return !(ep + 61 <= e1 && ep + 61 <= e2);
+}
+
+// Binary exponent k with max_abs * 2^-k in [0.5, 1) (0 for a zero or non-finite maximum),
+// clamped so that 2^k and 2^-k are finite
+__device__ __forceinline__ int jacobi_scale_exp(double max_abs) {
+  if (!(max_abs > 0.0) || !isfinite(max_abs)) return 0;
+  return min(1000, max(-1000, ilogb(max_abs) + 1));
 }
 
 // row-major rank e of the upper triangle (i <= j < half) -> (i, j); the float estimate
@@ -389,13 +421,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
                                                            double* evals, double* evecs,
                                                            double* work,
                                                            const int64_t* __restrict__ woffs,
-                                                           int max_m, double* flop_counter) {
+                                                           const int* __restrict__ ids,
+                                                           double* flop_counter) {
   extern __shared__ double smem[];
-  __shared__ int nrot;
+  __shared__ int nact[2];    // rotating pairs of the round (double-buffered by round parity)
+  __shared__ int nrot;       // rotations applied in the sweep
   long long rot_total = 0;   // thread 0: rotations applied
-  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int b = ids ? ids[blockIdx.x] : int(blockIdx.x), tid = threadIdx.x, nt = blockDim.x;
   const int m = dims[b];
-  if (m > max_m) return;   // left to k_jacobi_cluster
   const int mp = m + (m & 1), half = mp / 2;
   double *A, *Vt;
   double* next = smem;
@@ -415,101 +448,103 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
   double* sn = cs + half;
   int* pi_ = reinterpret_cast<int*>(sn + half);
   int* qi_ = pi_ + half;
-  int* perm = qi_ + half;
-  int* perm2 = perm + mp;
+  int* act = qi_ + half;
   const double* src = a + offs[b];
+  if (tid == 0) nact[0] = nact[1] = 0;
+  __shared__ double red[kJacobiThreads / 32];
+  // A scaled by 2^-ksc (exact) so that max |a| is in [0.5, 1); undone on the eigenvalues
+  const double amax = block_max_abs(src, m * m, red);
+  const int ksc = jacobi_scale_exp(amax);
+  const double sc = scalbn(1.0, -ksc);
   for (int e = tid; e < m * m; e += nt) {
-    A[e] = src[e];
+    A[e] = src[e] * sc;
     Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
   }
-  for (int i = tid; i < mp; i += nt) perm[i] = i;
-  __shared__ double red[kJacobiThreads / 32];
-  const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);
+  const long long tol_bits = __double_as_longlong(kJacobiAbsTol * (amax * sc));
+  __syncthreads();
   const int nblk = half * (half + 1) / 2;   // upper-triangle 2x2 blocks (i <= j)
+  int gr = 0;                               // rounds so far, over all sweeps
   for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
-    for (int round = 0; round < mp - 1; ++round) {
+    for (int round = 0; round < mp - 1; ++round, ++gr) {
+      const int par = gr & 1;
       for (int i = tid; i < half; i += nt) {
-        int p = perm[i], q = perm[mp - 1 - i];
+        int p = jacobi_at(i, round, mp), q = jacobi_at(mp - 1 - i, round, mp);
         if (p > q) { int x = p; p = q; q = x; }
         double c = 1.0, s = 0.0;
-        bool rot = false;
         if (q < m) {
-          double apq = A[p * m + q];
-          if (fabs(apq) > tol) {
-            double app = A[p * m + p], aqq = A[q * m + q];
-            double g = 100.0 * fabs(apq);
-            if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
-              jacobi_rotation(app, aqq, apq, c, s);
-              rot = true;
-            }
+          const double apq = A[p * m + q], app = A[p * m + p], aqq = A[q * m + q];
+          if (jacobi_rotates(app, aqq, apq, tol_bits)) {
+            jacobi_rotation(app, aqq, apq, c, s);
+            act[atomicAdd(&nact[par], 1)] = i;
           }
         }
         cs[i] = c;
         sn[i] = s;
         pi_[i] = p;
         qi_[i] = (q < m) ? q : -1;   // -1: p is unpaired this round (odd dimension)
-        if (rot) atomicAdd(&nrot, 1);
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block (pair i rows, pair j columns) per work item, i <= j
-      for (int e = tid; e < nblk; e += nt) {
-        // unrank e -> (i, j), 0 <= i <= j < half, row-major over the upper triangle
-        int i, j;
-        unrank_upper(e, half, i, j);
-        const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-        if (si == 0.0 && sj == 0.0) continue;   // identity on this block: nothing changes
-        const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
-        if (q >= 0 && u >= 0) {
-          double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
-          // rows: [c -s; s c] applied on (p, q); columns likewise on (r, u)
-          double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
-          double b21 = si * app + ci * aqp, b22 = si * apq + ci * aqq;
-          double n11 = cj * b11 - sj * b12, n12 = sj * b11 + cj * b12;
-          double n21 = cj * b21 - sj * b22, n22 = sj * b21 + cj * b22;
-          if (i == j && si != 0.0) { n12 = 0.0; n21 = 0.0; }
-          A[p * m + r] = n11; A[p * m + u] = n12; A[q * m + r] = n21; A[q * m + u] = n22;
-          if (i != j) {
-            A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
-          }
-        } else if (q >= 0) {   // column pair j is a single index r
-          double ap = A[p * m + r], aq = A[q * m + r];
-          double np = ci * ap - si * aq, nq = si * ap + ci * aq;
-          A[p * m + r] = np; A[q * m + r] = nq;
-          if (i != j) { A[r * m + p] = np; A[r * m + q] = nq; }
-        } else if (u >= 0) {   // row pair i is a single index p
-          double ar = A[p * m + r], au = A[p * m + u];
-          double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
-          A[p * m + r] = nr; A[p * m + u] = nu;
-          if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
-        }
+      const int na = nact[par];
+      if (tid == 0) {
+        nrot += na;
+        nact[par ^ 1] = 0;   // the next round's counter; its last reader was two rounds ago
       }
-      // V <- V J: rows p, q of V^T
-      for (int i = tid >> 5; i < half; i += nt >> 5) {
-        const int p = pi_[i], q = qi_[i];
-        const double c = cs[i], s = sn[i];
-        if (q < 0 || s == 0.0) continue;
-        for (int k = tid & 31; k < m; k += 32) {
+      if (na > 0) {
+        // A <- J^T A J, one 2x2 block (pair i rows, pair j columns) per work item, i <= j
+        for (int e = tid; e < nblk; e += nt) {
+          // unrank e -> (i, j), 0 <= i <= j < half, row-major over the upper triangle
+          int i, j;
+          unrank_upper(e, half, i, j);
+          const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+          if (si == 0.0 && sj == 0.0) continue;   // identity on this block: nothing changes
+          const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
+          if (q >= 0 && u >= 0) {
+            double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
+            // rows: [c -s; s c] applied on (p, q); columns likewise on (r, u)
+            double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
+            double b21 = si * app + ci * aqp, b22 = si * apq + ci * aqq;
+            double n11 = cj * b11 - sj * b12, n12 = sj * b11 + cj * b12;
+            double n21 = cj * b21 - sj * b22, n22 = sj * b21 + cj * b22;
+            if (i == j && si != 0.0) { n12 = 0.0; n21 = 0.0; }
+            A[p * m + r] = n11; A[p * m + u] = n12; A[q * m + r] = n21; A[q * m + u] = n22;
+            if (i != j) {
+              A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
+            }
+          } else if (q >= 0) {   // column pair j is a single index r
+            double ap = A[p * m + r], aq = A[q * m + r];
+            double np = ci * ap - si * aq, nq = si * ap + ci * aq;
+            A[p * m + r] = np; A[q * m + r] = nq;
+            if (i != j) { A[r * m + p] = np; A[r * m + q] = nq; }
+          } else if (u >= 0) {   // row pair i is a single index p
+            double ar = A[p * m + r], au = A[p * m + u];
+            double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
+            A[p * m + r] = nr; A[p * m + u] = nu;
+            if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
+          }
+        }
+        // V <- V J: rows p, q of V^T, one (rotating pair, column) per work item
+        for (int t = tid; t < na * m; t += nt) {
+          const int i = act[t / m], k = t % m;
+          const int p = pi_[i], q = qi_[i];
+          const double c = cs[i], s = sn[i];
           double vp = Vt[p * m + k], vq = Vt[q * m + k];
           Vt[p * m + k] = c * vp - s * vq;
           Vt[q * m + k] = s * vp + c * vq;
         }
       }
-      for (int i = tid; i < mp; i += nt)   // round-robin: keep perm[0], rotate the rest
-        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
-      __syncthreads();
-      for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
       __syncthreads();
     }
     if (tid == 0) rot_total += nrot;
     if (nrot == 0) break;
-    __syncthreads();
+    __syncthreads();   // every thread has read nrot before it is reset
   }
   if (flop_counter && tid == 0) atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
   // descending order, ties by index
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
+  const double unsc = scalbn(1.0, ksc);
   for (int i = tid; i < m; i += nt) {
     double di = A[i * m + i];
     int rank = 0;
@@ -517,78 +552,103 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
       double dj = A[j * m + j];
       rank += (dj > di) || (dj == di && j < i);
     }
-    ev[rank] = di;
+    ev[rank] = di * unsc;
     for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = Vt[i * m + k];
   }
 }
 
-// The same rotation sequence for one large matrix (dim > kJacobiClusterMin) spread over a
-// cluster of CTAs: GB300's FP64 rate per SM is low, so one SM per large matrix bounds the
+// The same rotation sequence for one matrix spread over a cluster of CTAs: GB300's FP64
+// rate per SM is low (about 1.75 operations per clock), so one SM per large matrix bounds the
 // whole truncation.  A and V^T stay in the global work space (L2 resident).  Every round,
 // each CTA computes all the round's rotations from its own copy of the round's pivots
-// (diagonal entries and pair off-diagonals, identical in every CTA), the CTAs update
-// disjoint 2 x 2 blocks of A and rows of V^T, and the thread that writes a pivot element of
-// the NEXT round also writes it into every CTA's pivot copy (double-buffered by round
-// parity); one cluster barrier per round then orders everything (the kernel is bound by
-// these barriers).  Each element sees the same operations in the same order as in
-// k_jacobi, so the results are identical.
-// One cluster per matrix: the grid is n_mat clusters, clusters of small matrices return at
-// once (uniformly, before any cluster barrier).
+// (diagonal entries and pair off-diagonals, identical in every CTA); the 2 x 2 blocks of A
+// are dealt out round-robin over the CTAs (block e to CTA e mod C) and the columns of V^T in
+// contiguous slices, so every CTA carries 1/C of the round's FP64 work; the thread that
+// writes a pivot element of the NEXT round also writes it into every CTA's pivot copy
+// (double-buffered by round parity); one cluster barrier per round then orders everything.
+// Each element sees the same operations in the same order as in k_jacobi, so the results
+// are identical.  One cluster per matrix: cluster k of the grid solves matrix ids[k].
 // barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
 // and distributed-shared-memory accesses of the cluster's threads around the barrier
 __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { cl.sync(); }
 
-__host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m) {
-  const int mp = m + (m & 1);
-  return size_t(mp) * (4 * sizeof(double) + 5 * sizeof(int));
+// shared memory of one CTA: rotations (c, s, p, q), the rotating-pair list, the pivot
+// copies of two rounds, the next round's pairing (partner and pair index of each row), the
+// eigenvalue ranks, and this CTA's column slice of V^T where it fits in kJacobiVsliceMax
+constexpr size_t kJacobiVsliceMax = 100 * 1024;
+__host__ __device__ inline size_t jacobi_cluster_aux_bytes(int m) {
+  const int mp = m + (m & 1), half = mp / 2;
+  return size_t(half) * (2 * sizeof(double) + 3 * sizeof(int)) +
+         size_t(2 * mp + 2 * half) * sizeof(double) + size_t(3 * mp) * sizeof(int);
+}
+__host__ __device__ inline size_t jacobi_vslice_bytes(int m, int C) {
+  return size_t(m) * size_t((m + C - 1) / C) * sizeof(double);
+}
+__host__ __device__ inline bool jacobi_vslice_in_smem(int m, int C) {
+  return jacobi_vslice_bytes(m, C) <= kJacobiVsliceMax;
+}
+__host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m, int C) {
+  const size_t aux = (jacobi_cluster_aux_bytes(m) + 15) / 16 * 16;
+  return aux + (jacobi_vslice_in_smem(m, C) ? jacobi_vslice_bytes(m, C) : 0);
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     const int* __restrict__ dims, const int64_t* __restrict__ offs,
     const int64_t* __restrict__ eoffs, const double* __restrict__ a, double* evals,
-    double* evecs, double* work, const int64_t* __restrict__ woffs, double* flop_counter) {
+    double* evecs, double* work, const int64_t* __restrict__ woffs,
+    const int* __restrict__ ids, double* flop_counter) {
   extern __shared__ double smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int C = int(cl.num_blocks());
   const int crank = int(cl.block_rank());
-  const int b = blockIdx.x / C;
+  const int b = ids[blockIdx.x / C];
   const int m = dims[b];
-  if (m <= kJacobiClusterMin) return;   // whole cluster: handled by k_jacobi
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int gt = crank * nt + tid, gn = C * nt;
   const int mp = m + (m & 1), half = mp / 2;
   double* A = work + woffs[b];
-  double* Vt = A + size_t(m) * m;
-  // shared: rotations of the round, and the pivots of the current and the next round
-  // (by parity: diagonal entries snd[par][x], pair off-diagonals sno[par][k]), written into
-  // every CTA of the cluster by the thread that updates the element
   double* cs = smem;
   double* sn = cs + half;
-  double* snd = sn + half;        // [2][mp]
-  double* sno = snd + 2 * mp;     // [2][half]
+  double* snd = sn + half;        // [2][mp]: diagonal entries, by round parity
+  double* sno = snd + 2 * mp;     // [2][half]: pair off-diagonals, by round parity
   int* pi_ = reinterpret_cast<int*>(sno + 2 * half);
   int* qi_ = pi_ + half;
-  int* perm = qi_ + half;
-  int* perm2 = perm + mp;
-  int* partner = perm2 + mp;      // partner of x in the next round's pairing
+  int* act = qi_ + half;
+  int* partner = act + half;      // partner of row x in the next round
   int* pidx = partner + mp;       // index of x's pair in the next round
+  int* rnk = pidx + mp;           // eigenvalue rank of row x (output)
+  // this CTA's columns [k0, k0 + ncol) of V^T: in shared memory (row x at Vs + x * ncol)
+  // where the slice fits, else in the global work space (row x at Vt + x * m + k0)
+  const int cw = (m + C - 1) / C;
+  const int k0 = min(m, crank * cw), ncol = min(m, k0 + cw) - k0;
+  const bool vs_smem = jacobi_vslice_in_smem(m, C);
+  double* Vs = smem + (jacobi_cluster_aux_bytes(m) + 15) / 16 * 2;
+  double* Vt = A + size_t(m) * m;
+  double* vrow = vs_smem ? Vs : Vt + k0;   // V^T[x][k0 + kk] = vrow[x * vld + kk]
+  const int vld = vs_smem ? ncol : m;
+  __shared__ int nact[2];
   __shared__ int nrot;
   long long rot_total = 0;   // thread 0: rotations applied
   const double* src = a + offs[b];
-  for (int e = gt; e < m * m; e += gn) {
-    A[e] = src[e];
-    Vt[e] = (e / m == e % m) ? 1.0 : 0.0;
-  }
-  for (int i = tid; i < mp; i += nt) perm[i] = i;
+  const int gt = crank * nt + tid, gn = C * nt;
+  if (tid == 0) nact[0] = nact[1] = 0;
   __shared__ double red[kJacobiThreads / 32];
-  const double tol = kJacobiAbsTol * block_max_abs(src, m * m, red);   // same in every CTA
-  cluster_barrier(cl);
-  // pivots of round 0 (pairs (k, mp-1-k)) from the now complete A, in every CTA
-  for (int x = tid; x < m; x += nt) snd[x] = A[x * m + x];
+  // A scaled by 2^-ksc (exact) so that max |a| is in [0.5, 1); the same in every CTA
+  const double amax = block_max_abs(src, m * m, red);
+  const int ksc = jacobi_scale_exp(amax);
+  const double sc = scalbn(1.0, -ksc);
+  const long long tol_bits = __double_as_longlong(kJacobiAbsTol * (amax * sc));
+  for (int e = gt; e < m * m; e += gn) A[e] = src[e] * sc;
+  for (int t = tid; t < m * ncol; t += nt) {
+    const int x = t / ncol, kk = t % ncol;
+    vrow[x * vld + kk] = (x == k0 + kk) ? 1.0 : 0.0;
+  }
+  // pivots of round 0 (pairs (k, mp-1-k)) from the input, in every CTA
+  for (int x = tid; x < m; x += nt) snd[x] = src[x * m + x] * sc;
   for (int k = tid; k < half; k += nt) {
     const int p = k, q = mp - 1 - k;
-    sno[k] = q < m ? A[p * m + q] : 0.0;
+    sno[k] = q < m ? src[p * m + q] * sc : 0.0;
   }
+  cluster_barrier(cl);   // A and V^T initialised by every CTA
   // element (x, y) of the updated A, v, into the next round's pivots of every CTA
   auto emit = [&](int np, int x, int y, double v) {
     double* dst = nullptr;
@@ -601,47 +661,43 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   };
   auto is_pivot = [&](int x, int y) { return x == y || partner[x] == y; };
   const int nblk = half * (half + 1) / 2;
-  int par = 0;
+  int gr = 0;   // rounds so far, over all sweeps
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
-    for (int round = 0; round < mp - 1; ++round) {
+    for (int round = 0; round < mp - 1; ++round, ++gr) {
+      const int par = gr & 1, np = par ^ 1;
       // rotations of the round from the local pivot copy (same values in every CTA)
       for (int i = tid; i < half; i += nt) {
-        int p = perm[i], q = perm[mp - 1 - i];
+        int p = jacobi_at(i, round, mp), q = jacobi_at(mp - 1 - i, round, mp);
         if (p > q) { int x = p; p = q; q = x; }
         double c = 1.0, s = 0.0;
-        bool rot = false;
         if (q < m) {
           const double apq = sno[par * half + i];
-          if (fabs(apq) > tol) {
-            const double app = snd[par * mp + p], aqq = snd[par * mp + q];
-            const double g = 100.0 * fabs(apq);
-            if (!(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
-              jacobi_rotation(app, aqq, apq, c, s);
-              rot = true;
-            }
+          const double app = snd[par * mp + p], aqq = snd[par * mp + q];
+          if (jacobi_rotates(app, aqq, apq, tol_bits)) {
+            jacobi_rotation(app, aqq, apq, c, s);
+            act[atomicAdd(&nact[par], 1)] = i;
           }
         }
         cs[i] = c;
         sn[i] = s;
         pi_[i] = p;
         qi_[i] = (q < m) ? q : -1;
-        if (rot) atomicAdd(&nrot, 1);
       }
-      for (int i = tid; i < mp; i += nt)
-        perm2[i] = (i == 0) ? perm[0] : (i == 1 ? perm[mp - 1] : perm[i - 1]);
-      __syncthreads();
-      for (int k = tid; k < half; k += nt) {
-        const int x = perm2[k], y = perm2[mp - 1 - k];
-        partner[x] = y;
-        partner[y] = x;
-        pidx[x] = k;
-        pidx[y] = k;
+      // pairing of the next round
+      for (int x = tid; x < mp; x += nt) {
+        const int pos = jacobi_pos(x, round + 1, mp);
+        partner[x] = jacobi_at(mp - 1 - pos, round + 1, mp);
+        pidx[x] = min(pos, mp - 1 - pos);
       }
       __syncthreads();
-      const int np = par ^ 1;
-      for (int e = gt; e < nblk; e += gn) {
+      const int na = nact[par];
+      if (tid == 0) {
+        nrot += na;
+        nact[np] = 0;   // the next round's counter; its last reader was two rounds ago
+      }
+      for (int e = crank + C * tid; e < nblk; e += C * nt) {
         int i, j;
         unrank_upper(e, half, i, j);
         const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
@@ -685,82 +741,74 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
           emit(np, p, u, nu);
         }
       }
-      for (int i = gt >> 5; i < half; i += gn >> 5) {
+      // V <- V J on this CTA's columns, one (rotating pair, column) per work item
+      for (int t = tid; t < na * ncol; t += nt) {
+        const int i = act[t / ncol], kk = t % ncol;
         const int p = pi_[i], q = qi_[i];
         const double c = cs[i], s = sn[i];
-        if (q < 0 || s == 0.0) continue;
-        for (int k = gt & 31; k < m; k += 32) {
-          double vp = Vt[p * m + k], vq = Vt[q * m + k];
-          Vt[p * m + k] = c * vp - s * vq;
-          Vt[q * m + k] = s * vp + c * vq;
-        }
+        double vp = vrow[p * vld + kk], vq = vrow[q * vld + kk];
+        vrow[p * vld + kk] = c * vp - s * vq;
+        vrow[q * vld + kk] = s * vp + c * vq;
       }
-      for (int i = tid; i < mp; i += nt) perm[i] = perm2[i];
       // one barrier per round: the next round reads only its own pivot copy, complete once
       // every CTA has passed this barrier, before any CTA updates A again
       cluster_barrier(cl);
-      par = np;
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
     if (tid == 0) rot_total += nrot;
     if (nrot == 0) break;
-    __syncthreads();
+    __syncthreads();   // every thread has read nrot before it is reset
   }
   if (flop_counter && crank == 0 && tid == 0)
     atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
+  // descending order, ties by index; every CTA ranks all rows and writes its own columns
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
-  for (int i = gt; i < m; i += gn) {
+  const double unsc = scalbn(1.0, ksc);
+  for (int i = tid; i < m; i += nt) {
     double di = A[i * m + i];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
       double dj = A[j * m + j];
       rank += (dj > di) || (dj == di && j < i);
     }
-    ev[rank] = di;
-    for (int k = 0; k < m; ++k) vec[int64_t(k) * m + rank] = Vt[i * m + k];
+    rnk[i] = rank;
+    if (crank == 0) ev[rank] = di * unsc;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * ncol; t += nt) {
+    const int x = t / ncol, kk = t % ncol;
+    vec[int64_t(k0 + kk) * m + rnk[x]] = vrow[x * vld + kk];
   }
 }
 
-void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
-                   const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster,
-                   double* flop_counter, const JacobiSide* side) {
-  if (n_mat <= 0) return;
-  const bool cluster = use_cluster && max_dim > kJacobiClusterMin;
-  // With a side stream, the one-CTA kernel (small matrices) runs there, concurrently with
-  // the cluster kernel (large ones) on s: they touch disjoint matrices and outputs.
-  cudaStream_t s_small = s;
-  if (cluster && side && side->stream) {
-    cudaEventRecord(side->fork, s);
-    cudaStreamWaitEvent(side->stream, side->fork, 0);
-    s_small = side->stream;
-  }
-  // the largest per-matrix need over every dimension up to max_dim
+// Both kernels' dynamic shared memory limits, set once: k_jacobi up to the largest
+// per-matrix need (dim 160: A in shared memory), k_jacobi_cluster up to the largest need
+// (a V^T slice of up to kJacobiVsliceMax) or the one-CTA-per-SM floor.  kJacobiSpreadSmem > half of an SM's 228 KB keeps a second CTA off the SM, so that
+// each CTA of a spread plan has an FP64 pipe to itself.
+constexpr size_t kJacobiSpreadSmem = 116 * 1024;
+static size_t jacobi_smem_limit() {
   size_t smem = 0;
-  const int single_max = cluster ? kJacobiClusterMin : max_dim;
-  for (int m = 1; m <= single_max; ++m)
-    smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
-  {
-    static std::mutex mu;
-    static size_t attr = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (smem > attr) {
-      cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      attr = smem;
-    }
-  }
-  k_jacobi<<<n_mat, kJacobiThreads, smem, s_small>>>(dims, offs, eoffs, a, evals, evecs, work,
-                                                      woffs, cluster ? kJacobiClusterMin : INT_MAX,
-                                                      flop_counter);
-  g_launches += 1;
-  if (!cluster) return;
-  // 16 CTAs per cluster where the device runs such clusters, else the portable 8
+  for (int m = 1; m <= 1024; ++m) smem = smem > jacobi_smem_bytes(m) ? smem : jacobi_smem_bytes(m);
+  return smem > kJacobiSpreadSmem ? smem : kJacobiSpreadSmem;
+}
+static size_t jacobi_cluster_smem_limit() {
+  size_t smem = kJacobiSpreadSmem;
+  for (int C = 2; C <= 16; C *= 2)
+    for (int m = 1; m <= 1024; ++m) smem = std::max(smem, jacobi_cluster_smem_bytes(m, C));
+  return smem;
+}
+
+// Largest cluster size the device runs for k_jacobi_cluster with spread shared memory: 16
+// (non-portable) where possible, else 8.
+static int jacobi_max_cluster() {
   static std::once_flag once;
   static int csize = 8;
   std::call_once(once, [] {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(jacobi_smem_limit()));
     cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(jacobi_cluster_smem_bytes(1024)));
+                         int(jacobi_cluster_smem_limit()));
     if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
         cudaSuccess) {
       cudaGetLastError();
@@ -769,7 +817,7 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
     cudaLaunchConfig_t q = {};
     q.gridDim = dim3(16, 1, 1);
     q.blockDim = dim3(kJacobiThreads, 1, 1);
-    q.dynamicSmemBytes = jacobi_cluster_smem_bytes(1024);
+    q.dynamicSmemBytes = kJacobiSpreadSmem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 16;
@@ -783,25 +831,136 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
       csize = 16;
     cudaGetLastError();
   });
-  const int kc = csize;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(n_mat) * kc, 1, 1);
-  cfg.blockDim = dim3(kJacobiThreads, 1, 1);
-  cfg.dynamicSmemBytes = jacobi_cluster_smem_bytes(max_dim);
-  cfg.stream = s;
-  cudaLaunchAttribute attr_c[1];
-  attr_c[0].id = cudaLaunchAttributeClusterDimension;
-  attr_c[0].val.clusterDim.x = kc;
-  attr_c[0].val.clusterDim.y = 1;
-  attr_c[0].val.clusterDim.z = 1;
-  cfg.attrs = attr_c;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs,
-                     flop_counter);
+  return csize;
+}
+
+void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
+                   const double* a, double* evals, double* evecs, double* work,
+                   const int64_t* woffs, int max_dim, cudaStream_t s, double* flop_counter) {
+  if (n_mat <= 0) return;
+  jacobi_max_cluster();   // sets the shared memory limits
+  // the need is not monotonic in the dimension (V^T leaves shared memory above
+  // kJacobiSmemAV, A above kJacobiSmemA): the largest over every dimension up to max_dim
+  size_t smem = 0;
+  for (int m = 1; m <= max_dim; ++m) smem = std::max(smem, jacobi_smem_bytes(m));
+  k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
+                                               nullptr, flop_counter);
   g_launches += 1;
-  if (s_small != s) {   // join: s waits for the one-CTA kernel
-    cudaEventRecord(side->join, s_small);
-    cudaStreamWaitEvent(s, side->join, 0);
+}
+
+// Modelled time of one Jacobi round (us) of an m x m matrix on a cluster of C CTAs, one
+// per SM: the A and V^T updates (about 4 m^2 FP64 operations, split over the CTAs), the
+// m/2 rotations that every CTA computes (about 35 operations each), at 1.75 operations per
+// clock at 2.07 GHz, plus the round's synchronisation (a cluster barrier, or __syncthreads).
+static double jacobi_round_us(int m, int C) {
+  const double ops = 4.0 * m * m / C + 17.5 * m;
+  return ops / 3600.0 + (C > 1 ? 1.0 : 0.3);
+}
+
+JacobiPlan plan_jacobi(const std::vector<int>& dims) {
+  JacobiPlan p;
+  const int n = int(dims.size());
+  p.csize.assign(n, 1);
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int cmax = jacobi_max_cluster();
+  // CTAs left for doubling: a seventh of the SMs stays free, as clusters must be packed
+  // into GPCs (up to 16 SMs of one GPC per cluster)
+  const long long budget = n_sm - n_sm / 7;
+  long long used = n;
+  if (used <= budget) {
+    // rounds per sweep (m - 1) x round time: the sweep count is similar across a batch.
+    // Double the cluster of the slowest matrix that still gains from it, while the CTAs fit.
+    auto t = [&](int b, int C) { return double(dims[b]) * jacobi_round_us(dims[b], C); };
+    for (;;) {
+      int w = -1;
+      double tw = -1.0;
+      for (int b = 0; b < n; ++b) {
+        const int C = p.csize[b];
+        const double tb = t(b, C);
+        if (C < cmax && used + C <= budget && t(b, 2 * C) < tb && tb > tw) {
+          tw = tb;
+          w = b;
+        }
+      }
+      if (w < 0) break;
+      used += p.csize[w];
+      p.csize[w] *= 2;
+    }
+    p.spread = true;
+  }
+  static const int kSizes[kJacobiClasses] = {16, 8, 4, 2, 1};   // launch order
+  for (int k = 0; k < kJacobiClasses; ++k) {
+    const int begin = int(p.ids.size());
+    size_t smem = 0;
+    for (int b = 0; b < n; ++b)
+      if (p.csize[b] == kSizes[k]) {
+        p.ids.push_back(b);
+        smem = std::max(smem, kSizes[k] == 1 ? jacobi_smem_bytes(dims[b])
+                                             : jacobi_cluster_smem_bytes(dims[b], kSizes[k]));
+      }
+    if (int(p.ids.size()) == begin) continue;
+    if (p.spread) smem = std::max(smem, kJacobiSpreadSmem);
+    p.cls_csize[p.n_cls] = kSizes[k];
+    p.cls_begin[p.n_cls] = begin;
+    p.cls_smem[p.n_cls] = smem;
+    ++p.n_cls;
+  }
+  p.cls_begin[p.n_cls] = int(p.ids.size());
+  return p;
+}
+
+void launch_jacobi_plan(const JacobiPlan& p, const int* ids, const int* dims, const int64_t* offs,
+                        const int64_t* eoffs, const double* a, double* evals, double* evecs,
+                        double* work, const int64_t* woffs, cudaStream_t s,
+                        const JacobiStreams* side, double* flop_counter) {
+  if (p.n_cls == 0) return;
+  jacobi_max_cluster();
+  // With side streams, class 0 (the largest clusters) runs on side stream 0, which has the
+  // highest priority so that its clusters find whole GPCs free, class 1 on s, class k >= 2 on
+  // side stream k - 1: they touch disjoint matrices and outputs.
+  const bool fork = side && p.n_cls > 1;
+  auto stream_of = [&](int k) { return !fork ? s : (k == 1 ? s : side->stream[k == 0 ? 0 : k - 1]); };
+  if (fork) {
+    cudaEventRecord(side->fork, s);
+    for (int k = 0; k < p.n_cls; ++k)
+      if (k != 1) cudaStreamWaitEvent(stream_of(k), side->fork, 0);
+  }
+  for (int k = 0; k < p.n_cls; ++k) {
+    cudaStream_t sk = stream_of(k);
+    const int C = p.cls_csize[k];
+    const int cnt = p.cls_begin[k + 1] - p.cls_begin[k];
+    const int* cids = ids + p.cls_begin[k];
+    const size_t smem = p.cls_smem[k];
+    if (C == 1) {
+      k_jacobi<<<cnt, kJacobiThreads, smem, sk>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
+                                                  cids, flop_counter);
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(cnt) * unsigned(C), 1, 1);
+      cfg.blockDim = dim3(kJacobiThreads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = sk;
+      cudaLaunchAttribute attr_c[1];
+      attr_c[0].id = cudaLaunchAttributeClusterDimension;
+      attr_c[0].val.clusterDim.x = unsigned(C);
+      attr_c[0].val.clusterDim.y = 1;
+      attr_c[0].val.clusterDim.z = 1;
+      cfg.attrs = attr_c;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs,
+                         cids, flop_counter);
+    }
+    g_launches += 1;
+  }
+  if (fork) {   // join: s waits for every class on a side stream
+    for (int k = 0; k < p.n_cls; ++k) {
+      if (k == 1) continue;
+      const int j = k == 0 ? 0 : k - 1;
+      cudaEventRecord(side->join[j], side->stream[j]);
+      cudaStreamWaitEvent(s, side->join[j], 0);
+    }
   }
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace b2k {
 
@@ -128,28 +129,50 @@ void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const 
 void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
                  const double* R, double* diag, cudaStream_t s);
 void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s);
-// Batched symmetric eigensolver; offs/eoffs: element offsets of each matrix (dims^2 each)
-// and of its eigenvalues; work/woffs: global work space of 2 dims^2 doubles for each
-// matrix with jacobi_needs_work(dims, use_cluster) (the others work in shared memory).
-// With use_cluster, matrices with dims > kJacobiClusterMin are solved by a cluster of 16
-// CTAs (8 where the device cannot run 16) each, with the same rotations and results as
-// one CTA; the others by one CTA each.
+// Batched symmetric eigensolver (cyclic Jacobi); offs/eoffs: element offsets of each
+// matrix (dims^2 each) and of its eigenvalues; work/woffs: global work space of 2 dims^2
+// doubles for each matrix with jacobi_needs_work(dims, cluster size) (the others work in
+// shared memory).  A matrix is solved either by one CTA or by a cluster of 2 to 16 CTAs;
+// every cluster size applies the same rotations in the same order, so the results are
+// identical (bitwise) whichever size solves a matrix.
 constexpr int kJacobiSmemAV = 112;
-constexpr int kJacobiClusterMin = 64;
-// Optional second stream (with a fork and a join event) on which the one-CTA kernel runs
-// concurrently with the cluster kernel.
-struct JacobiSide {
-  cudaStream_t stream;
-  cudaEvent_t fork, join;
-};
-inline bool jacobi_needs_work(int dim, bool use_cluster = true) {
-  return dim > (use_cluster ? kJacobiClusterMin : kJacobiSmemAV);
-}
+inline bool jacobi_needs_work(int dim, int csize) { return csize > 1 || dim > kJacobiSmemAV; }
+// One CTA per matrix, on stream s.
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s, bool use_cluster = true,
-                   double* flop_counter = nullptr,   // += 18 m per applied rotation
-                   const JacobiSide* side = nullptr);
+                   const int64_t* woffs, int max_dim, cudaStream_t s,
+                   double* flop_counter = nullptr);   // += 18 m per applied rotation
+// Host-side plan of a batch: a cluster size per matrix and the matrices grouped by size
+// (ids, class by class).  GB300 runs FP64 at ~1.75 FMA per clock per SM, so one CTA is
+// arithmetic-bound on a large matrix; the plan starts from one CTA per matrix and keeps
+// doubling the cluster of the matrix with the longest modelled time while the CTAs still
+// fit one per SM.  With more matrices than SMs every matrix keeps one CTA.
+constexpr int kJacobiClasses = 5;   // cluster sizes 1, 2, 4, 8, 16
+struct JacobiPlan {
+  std::vector<int> csize;   // per matrix
+  std::vector<int> ids;     // matrix ids ordered by class
+  int n_cls = 0;
+  int cls_csize[kJacobiClasses] = {};
+  int cls_begin[kJacobiClasses + 1] = {};
+  size_t cls_smem[kJacobiClasses] = {};   // dynamic shared memory of each class's launch
+  bool spread = false;      // total CTAs <= SMs: launched one CTA per SM
+};
+JacobiPlan plan_jacobi(const std::vector<int>& dims);
+// Streams for the classes of a plan, forked from the caller's stream s and joined back into
+// it: class 0 (largest clusters) on stream[0], which should have the highest priority, class
+// 1 on s, class k >= 2 on stream[k - 1].
+struct JacobiStreams {
+  cudaStream_t stream[kJacobiClasses - 1];
+  cudaEvent_t fork;
+  cudaEvent_t join[kJacobiClasses - 1];
+};
+// ids: device copy of plan.ids.  Without side streams the classes run one after another
+// on s.
+void launch_jacobi_plan(const JacobiPlan& plan, const int* ids, const int* dims,
+                        const int64_t* offs, const int64_t* eoffs, const double* a,
+                        double* evals, double* evecs, double* work, const int64_t* woffs,
+                        cudaStream_t s, const JacobiStreams* side = nullptr,
+                        double* flop_counter = nullptr);
 // Global top-M selection over n eigenvalues (sector-major, descending in each sector).
 // sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
 // (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.

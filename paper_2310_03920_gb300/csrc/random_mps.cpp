@@ -11,7 +11,8 @@
 // seed + counter, Box-Muller), counter = position of the entry in the concatenated site
 // data.  Right-orthonormal form on the GPU: for site k = n-1 .. 1 and each left sector j,
 // G = X X^T over the sector's row block X, G = U diag(lam) U^T (batched Jacobi kernel),
-// B = diag(lam^-1/2) U^T X, and U diag(lam^1/2) is multiplied into site k-1.  Site 0 is
+// B = diag(lam^-1/2) U^T X, and U diag(lam^1/2) is multiplied into site k-1; done twice per
+// site, so that the orthonormality error is not the first pass's 1e-15 / min(lam).  Site 0 is
 // scaled to unit norm.
 #include <algorithm>
 #include <cmath>
@@ -181,9 +182,11 @@ b2_mps_s* b2_mps_random_impl(b2::Ctx* ctx, b2_mpo_s* mpo, int M, const double* o
     for (int64_t i = 0; i < st.size; ++i) h[size_t(i)] = gaussian(seed, counter++);
     b2::upload(ctx, st.data, h);
   }
-  // right-orthonormalise sites n-1 .. 1
+  // right-orthonormalise sites n-1 .. 1; two passes per site: the first leaves B B^T - I at
+  // about 1e-15 / lam_min of the Gram matrix, the second (Gram matrix ~ I) at rounding level
   using b2k::GemmTerm;
-  for (int k = n - 1; k >= 1; --k) {
+  for (int k = n - 1; k >= 1; --k)
+  for (int pass = 0; pass < 2; ++pass) {
     auto& st = mps->sites[k];
     const Bond& bl = mps->bonds[k];
     // G_j = X_j X_j^T for every left sector j, stored consecutively
@@ -223,25 +226,7 @@ b2_mps_s* b2_mps_random_impl(b2::Ctx* ctx, b2_mpo_s* mpo, int M, const double* o
     bt.p[1] = G.as<double>();
     pg.launch(ctx, bt);
     // eigen-decomposition of every G_j
-    std::vector<int64_t> woff(bl.size(), 0);
-    int64_t wsize = 0;
-    int max_dim = 0;
-    for (int j = 0; j < bl.size(); ++j) {
-      max_dim = std::max(max_dim, dims[j]);
-      if (b2k::jacobi_needs_work(dims[j])) {
-        woff[j] = wsize;
-        wsize += 2 * int64_t(dims[j]) * dims[j];
-      }
-    }
-    b2::DevBuf d_dims, d_goff, d_eoff, d_woff, work;
-    b2::upload(ctx, d_dims, dims);
-    b2::upload(ctx, d_goff, goff);
-    b2::upload(ctx, d_eoff, eoff);
-    b2::upload(ctx, d_woff, woff);
-    if (wsize) work.reset(ctx, sizeof(double) * wsize);
-    b2k::launch_jacobi(bl.size(), d_dims.as<int>(), d_goff.as<int64_t>(), d_eoff.as<int64_t>(),
-                       G.as<double>(), lam.as<double>(), U.as<double>(), work.as<double>(),
-                       d_woff.as<int64_t>(), max_dim, ctx->stream);
+    b2::eigh_batched(ctx, dims, goff, eoff, G.as<double>(), lam.as<double>(), U.as<double>());
     for (int j = 0; j < bl.size(); ++j) {
       b2k::launch_scale_cols(dims[j], U.as<double>() + goff[j], lam.as<double>() + eoff[j], -0.5,
                              1e-300, U1.as<double>() + goff[j], ctx->stream);

@@ -90,7 +90,7 @@ extern "C" int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, co
     const int64_t* d_eoffs = reinterpret_cast<const int64_t*>(meta + offsetof(Meta, eoffs));
     const int64_t* d_woffs = reinterpret_cast<const int64_t*>(meta + offsetof(Meta, woffs));
     b2k::launch_jacobi(n_mat, d_dims, d_offs, d_eoffs, a, evals, evecs, base + kMetaDoubles,
-                       d_woffs, max_dim, ctx->c.stream, /*use_cluster=*/false);
+                       d_woffs, max_dim, ctx->c.stream);
     B2_CUDA(cudaGetLastError());
     return B2_OK;
   } catch (const b2::Error& err) {

@@ -75,12 +75,18 @@ def test_static_eigh_rejects_requests_beyond_its_scratch():
     ctx.close()
 
 
-def test_cluster_jacobi_matches_single_cta_bitwise():
-    # b2_eigh_batched solves matrices with dim > 64 on a CTA cluster; the static entry
-    # point keeps one CTA per matrix.  Both apply the same rotations in the same order.
+# the second batch is shaped like one truncation step of the L = 32, M = 500 Hubbard sweep
+# (43 sectors, dims 147 down to 2): its plan uses every cluster size, 16, 8, 4, 2 and 1
+@pytest.mark.parametrize("dims", [
+    [64, 65, 90, 112, 113, 160, 201, 300],
+    [147, 116, 110, 104] + [int(x) for x in np.linspace(100, 2, 39)],
+])
+def test_cluster_jacobi_matches_single_cta_bitwise(dims):
+    # b2_eigh_batched gives each matrix one CTA or a cluster of 2 to 16 CTAs (a plan made on
+    # the host from the dims); the static entry point keeps one CTA per matrix.  All apply
+    # the same rotations in the same order.
     ctx = b2.Context(0)
     rng = np.random.default_rng(43)
-    dims = [64, 65, 90, 112, 113, 160, 201, 300]
     mats, flat = _batch(rng, dims)
     ev_c, vec_c = _run(b2.b2_eigh_batched, ctx, dims, flat)
     ev_s, vec_s = _run(b2.b2_eigh_batched_static, ctx, dims, flat)
