@@ -297,9 +297,9 @@ int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri
 
 /* ------------------------------------------------------------------------ profiling
  * Measurement support for benchmarks (no counterpart in the paper).  While enabled, every
- * launch of the H_eff contraction kernel, of the truncation eigensolver and of the Davidson
- * Rayleigh-Ritz eigensolver is bracketed by CUDA events on the context stream, and every
- * kernel launch of the library is counted.
+ * launch of the H_eff contraction kernel, of the truncation eigensolver (inside sweeps and
+ * b2_eigh_batched) and of the Davidson Rayleigh-Ritz eigensolver is bracketed by CUDA events
+ * on the context stream, and every kernel launch of the library is counted.
  * b2_profile(ctx, 1) also resets the counters. */
 typedef struct {
   int64_t launches;        /* kernel launches of the library since the reset */

@@ -296,7 +296,17 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
       o += int64_t(d[i]) * d[i];
       e += d[i];
     }
-    b2::eigh_batched(c, d, offs, eoffs, a, evals, evecs);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+      B2_CUDA(cudaEventCreate(&e0));
+      B2_CUDA(cudaEventCreate(&e1));
+      B2_CUDA(cudaEventRecord(e0, c->stream));
+    }
+    b2::eigh_batched(c, d, offs, eoffs, a, evals, evecs, c->prof ? c->d_eig_flops : nullptr);
+    if (c->prof) {
+      B2_CUDA(cudaEventRecord(e1, c->stream));
+      c->eig_events.push_back({e0, e1});
+    }
     B2_CUDA(cudaGetLastError());
     B2_CUDA(cudaStreamSynchronize(c->stream));
   });
