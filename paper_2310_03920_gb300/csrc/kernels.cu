@@ -636,6 +636,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
 // barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
 // and distributed-shared-memory accesses of the cluster's threads around the barrier
 __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { cl.sync(); }
+// the same barrier split in two: work between arrive and wait overlaps the other CTAs'
+// arrival (it must not touch memory that other CTAs read after the barrier)
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // shared memory of one CTA: rotations (c, s, p, q), the rotating-pair list, the pivot
 // copies of two rounds, the next round's pairing (partner and pair index of each row), the
@@ -832,6 +840,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
           emit(np, p, u, nu);
         }
       }
+      // one barrier per round: the next round reads only its own pivot copy, complete once
+      // every CTA has passed this barrier, before any CTA updates A again.  The V^T slice
+      // is this CTA's alone, so its update runs between arrive and wait; the CTA barrier
+      // after it keeps the next round's rotations from overwriting what it still reads.
+      cluster_arrive_release();
       // V <- V J on this CTA's columns, one (rotating pair, column) per work item
       for (int t = tid; t < na * ncol; t += nt) {
         const int i = act[t / ncol], kk = t % ncol;
@@ -841,9 +854,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
         vrow[p * vld + kk] = c * vp - s * vq;
         vrow[q * vld + kk] = s * vp + c * vq;
       }
-      // one barrier per round: the next round reads only its own pivot copy, complete once
-      // every CTA has passed this barrier, before any CTA updates A again
-      cluster_barrier(cl);
+      __syncthreads();
+      cluster_wait_acquire();
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
     if (tid == 0) rot_total += nrot;
