@@ -647,8 +647,9 @@ __device__ __forceinline__ void cluster_wait_acquire() {
 
 // shared memory of one CTA: rotations (c, s, p, q), the rotating-pair list, the pivot
 // copies of two rounds, the next round's pairing (partner and pair index of each row), the
-// eigenvalue ranks, the sweep's active rows (flags, list, positions), and this CTA's column
-// slice of V^T where it fits in kJacobiVsliceMax
+// eigenvalue ranks, the sweep's active rows (flags, list, positions), this CTA's column
+// slice of V^T where it fits in kJacobiVsliceMax and its rows of A where they fit in
+// kJacobiAsliceMax
 constexpr size_t kJacobiVsliceMax = 100 * 1024;
 __host__ __device__ inline size_t jacobi_cluster_aux_bytes(int m) {
   const int mp = m + (m & 1), half = mp / 2;
@@ -661,9 +662,19 @@ __host__ __device__ inline size_t jacobi_vslice_bytes(int m, int C) {
 __host__ __device__ inline bool jacobi_vslice_in_smem(int m, int C) {
   return jacobi_vslice_bytes(m, C) <= kJacobiVsliceMax;
 }
+// A distributed over the cluster's shared memory by rows (row x in CTA x mod C, local row
+// x / C) where the slice fits in kJacobiAsliceMax; else A stays in the global work space
+constexpr size_t kJacobiAsliceMax = 96 * 1024;
+__host__ __device__ inline size_t jacobi_aslice_bytes(int m, int C) {
+  return size_t((m + C - 1) / C) * size_t(m) * sizeof(double);
+}
+__host__ __device__ inline bool jacobi_aslice_in_smem(int m, int C) {
+  return jacobi_aslice_bytes(m, C) <= kJacobiAsliceMax;
+}
 __host__ __device__ inline size_t jacobi_cluster_smem_bytes(int m, int C) {
   const size_t aux = (jacobi_cluster_aux_bytes(m) + 15) / 16 * 16;
-  return aux + (jacobi_vslice_in_smem(m, C) ? jacobi_vslice_bytes(m, C) : 0);
+  return aux + (jacobi_vslice_in_smem(m, C) ? jacobi_vslice_bytes(m, C) : 0) +
+         (jacobi_aslice_in_smem(m, C) ? jacobi_aslice_bytes(m, C) : 0);
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   const int m = dims[b];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mp = m + (m & 1), half = mp / 2;
-  double* A = work + woffs[b];
+  double* Ag = work + woffs[b];
   double* cs = smem;
   double* sn = cs + half;
   double* snd = sn + half;        // [2][mp]: diagonal entries, by round parity
@@ -700,9 +711,16 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   const int k0 = min(m, crank * cw), ncol = min(m, k0 + cw) - k0;
   const bool vs_smem = jacobi_vslice_in_smem(m, C);
   double* Vs = smem + (jacobi_cluster_aux_bytes(m) + 15) / 16 * 2;
-  double* Vt = A + size_t(m) * m;
+  double* Vt = Ag + size_t(m) * m;
   double* vrow = vs_smem ? Vs : Vt + k0;   // V^T[x][k0 + kk] = vrow[x * vld + kk]
   const int vld = vs_smem ? ncol : m;
+  // element (x, y) of A: row x of CTA x mod C in distributed shared memory, or global
+  const bool as_smem = jacobi_aslice_in_smem(m, C);
+  double* As = Vs + (vs_smem ? size_t(m) * cw : 0);   // the same offset in every CTA
+  auto aref = [&](int x, int y) -> double* {
+    if (as_smem) return cl.map_shared_rank(As + size_t(x / C) * m + y, x % C);
+    return Ag + size_t(x) * m + y;
+  };
   __shared__ int nact[2];
   __shared__ int nrot;
   long long rot_total = 0;   // thread 0: rotations applied
@@ -715,7 +733,15 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   const int ksc = jacobi_scale_exp(amax);
   const double sc = scalbn(1.0, -ksc);
   const long long tol_bits = __double_as_longlong(kJacobiAbsTol * (amax * sc));
-  for (int e = gt; e < m * m; e += gn) A[e] = src[e] * sc;
+  if (as_smem) {   // this CTA's rows x = crank, crank + C, ...
+    const int nr = (m - crank + C - 1) / C;
+    for (int t = tid; t < nr * m; t += nt) {
+      const int lx = t / m, y = t % m;
+      As[size_t(lx) * m + y] = src[size_t(lx * C + crank) * m + y] * sc;
+    }
+  } else {
+    for (int e = gt; e < m * m; e += gn) Ag[e] = src[e] * sc;
+  }
   for (int t = tid; t < m * ncol; t += nt) {
     const int x = t / ncol, kk = t % ncol;
     vrow[x * vld + kk] = (x == k0 + kk) ? 1.0 : 0.0;
@@ -737,7 +763,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     // active rows (deflation): this CTA checks rows crank, crank + C, ... and writes the
     // flags into every CTA; all CTAs then hold the same flags and build the same list
     for (int x = crank + C * tid; x < m; x += C * nt) {
-      const int u = jacobi_row_active(A + x * m, x, m, tol_bits);
+      const int u = jacobi_row_active(as_smem ? As + size_t(x / C) * m : Ag + size_t(x) * m,
+                                      x, m, tol_bits);
       for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(uc + x, rk) = u;
     }
     cluster_barrier(cl);
@@ -748,11 +775,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     // pivots of the sweep's first round from A, in every CTA
     {
       const int par = gr & 1;
-      for (int x = tid; x < m; x += nt) snd[par * mp + x] = A[x * m + x];
+      for (int x = tid; x < m; x += nt) snd[par * mp + x] = *aref(x, x);
       for (int k = tid; k < hs; k += nt) {
         int pa = jacobi_at(k, 0, msp), pb = jacobi_at(msp - 1 - k, 0, msp);
         if (pa > pb) { int x = pa; pa = pb; pb = x; }
-        sno[par * half + k] = pb < ms ? A[sidx[pa] * m + sidx[pb]] : 0.0;
+        sno[par * half + k] = pb < ms ? *aref(sidx[pa], sidx[pb]) : 0.0;
       }
     }
     if (tid == 0) nrot = 0;
@@ -802,40 +829,48 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
         const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
         const int p = pi_[i], q = qi_[i], r = pi_[j], u = qi_[j];
         if (si == 0.0 && sj == 0.0) {   // identity on this block: only pass on its pivots
-          if (is_pivot(p, r)) emit(np, p, r, A[p * m + r]);
-          if (u >= 0 && is_pivot(p, u)) emit(np, p, u, A[p * m + u]);
-          if (q >= 0 && is_pivot(q, r)) emit(np, q, r, A[q * m + r]);
-          if (q >= 0 && u >= 0 && i != j && is_pivot(q, u)) emit(np, q, u, A[q * m + u]);
-          if (i == j && q >= 0) emit(np, q, q, A[q * m + q]);
+          if (is_pivot(p, r)) emit(np, p, r, *aref(p, r));
+          if (u >= 0 && is_pivot(p, u)) emit(np, p, u, *aref(p, u));
+          if (q >= 0 && is_pivot(q, r)) emit(np, q, r, *aref(q, r));
+          if (q >= 0 && u >= 0 && i != j && is_pivot(q, u)) emit(np, q, u, *aref(q, u));
+          if (i == j && q >= 0) emit(np, q, q, *aref(q, q));
           continue;
         }
         if (q >= 0 && u >= 0) {
-          double app = A[p * m + r], apq = A[p * m + u], aqp = A[q * m + r], aqq = A[q * m + u];
+          double* const ppr = aref(p, r);
+          double* const ppu = aref(p, u);
+          double* const pqr = aref(q, r);
+          double* const pqu = aref(q, u);
+          double app = *ppr, apq = *ppu, aqp = *pqr, aqq = *pqu;
           double b11 = ci * app - si * aqp, b12 = ci * apq - si * aqq;
           double b21 = si * app + ci * aqp, b22 = si * apq + ci * aqq;
           double n11 = cj * b11 - sj * b12, n12 = sj * b11 + cj * b12;
           double n21 = cj * b21 - sj * b22, n22 = sj * b21 + cj * b22;
           if (i == j && si != 0.0) { n12 = 0.0; n21 = 0.0; }
-          A[p * m + r] = n11; A[p * m + u] = n12; A[q * m + r] = n21; A[q * m + u] = n22;
+          *ppr = n11; *ppu = n12; *pqr = n21; *pqu = n22;
           if (i != j) {
-            A[r * m + p] = n11; A[u * m + p] = n12; A[r * m + q] = n21; A[u * m + q] = n22;
+            *aref(r, p) = n11; *aref(u, p) = n12; *aref(r, q) = n21; *aref(u, q) = n22;
           }
           emit(np, p, r, n11);
           emit(np, p, u, n12);
           if (i != j) emit(np, q, r, n21);   // (q, p) of a diagonal block is (p, q)
           emit(np, q, u, n22);
         } else if (q >= 0) {
-          double ap = A[p * m + r], aq = A[q * m + r];
+          double* const ppr = aref(p, r);
+          double* const pqr = aref(q, r);
+          double ap = *ppr, aq = *pqr;
           double np_ = ci * ap - si * aq, nq = si * ap + ci * aq;
-          A[p * m + r] = np_; A[q * m + r] = nq;
-          if (i != j) { A[r * m + p] = np_; A[r * m + q] = nq; }
+          *ppr = np_; *pqr = nq;
+          if (i != j) { *aref(r, p) = np_; *aref(r, q) = nq; }
           emit(np, p, r, np_);
           emit(np, q, r, nq);
         } else if (u >= 0) {
-          double ar = A[p * m + r], au = A[p * m + u];
+          double* const ppr = aref(p, r);
+          double* const ppu = aref(p, u);
+          double ar = *ppr, au = *ppu;
           double nr = cj * ar - sj * au, nu = sj * ar + cj * au;
-          A[p * m + r] = nr; A[p * m + u] = nu;
-          if (i != j) { A[r * m + p] = nr; A[u * m + p] = nu; }
+          *ppr = nr; *ppu = nu;
+          if (i != j) { *aref(r, p) = nr; *aref(u, p) = nu; }
           emit(np, p, r, nr);
           emit(np, p, u, nu);
         }
@@ -868,11 +903,16 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
   const double unsc = scalbn(1.0, ksc);
+  // the diagonal, gathered into the pivot buffer (all of it read by every thread); the
+  // barrier keeps every CTA's rows of A alive until all CTAs have read them
+  double* dg = snd;
+  for (int x = tid; x < m; x += nt) dg[x] = *aref(x, x);
+  cluster_barrier(cl);
   for (int i = tid; i < m; i += nt) {
-    double di = A[i * m + i];
+    double di = dg[i];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      double dj = A[j * m + j];
+      double dj = dg[j];
       rank += (dj > di) || (dj == di && j < i);
     }
     rnk[i] = rank;
@@ -896,7 +936,7 @@ static size_t jacobi_smem_limit() {
   return smem > kJacobiSpreadSmem ? smem : kJacobiSpreadSmem;
 }
 static size_t jacobi_cluster_smem_limit() {
-  size_t smem = kJacobiSpreadSmem;
+  size_t smem = kJacobiSpreadSmem;   // at most aux + kJacobiVsliceMax + kJacobiAsliceMax
   for (int C = 2; C <= 16; C *= 2)
     for (int m = 1; m <= 1024; ++m) smem = std::max(smem, jacobi_cluster_smem_bytes(m, C));
   return smem;
