@@ -290,17 +290,17 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 // ================================================================ batched Jacobi
 // Cyclic Jacobi for a real symmetric matrix (Golub & Van Loan, Matrix Computations,
 // Alg. 8.5.2 / 8.5.3 "sym.schur2" rotation), one CTA per matrix.  Each sweep visits every
-// pivot pair once in round-robin order, m/2 disjoint pairs per round, so one round applies
-// the block-diagonal rotation J (2 x 2 blocks on the pairs) as A <- J^T A J.  Element
-// blocks A[{p_i, q_i}][{p_j, q_j}] depend only on their own four entries, so a round is
-// one pass over the 2 x 2 blocks of the upper triangle (mirrored below), and the
-// eigenvector matrix is kept transposed (V^T) so that its rotations update two contiguous
-// rows.  A rotation is skipped when the off-diagonal element is below kJacobiAbsTol times
-// the largest input element or negligible next to both diagonal entries (100|a_pq| adds
-// nothing to |a_pp| nor |a_qq|); the iteration stops after a sweep without rotations (at
-// most kMaxSweeps sweeps).  A lives in shared memory for
-// dim <= kJacobiSmemA, V^T too for dim <= kJacobiSmemAV; larger matrices use global work
-// space (2 dim^2 doubles).
+// pair of its active rows (rows that still hold an off-diagonal element above the
+// threshold) once in round-robin order, disjoint pairs per round, so one round applies the
+// block-diagonal rotation J (2 x 2 blocks on the pairs) as A <- J^T A J.  Element blocks
+// A[{p_i, q_i}][{p_j, q_j}] depend only on their own four entries, so a round is one pass
+// over the 2 x 2 blocks of the upper triangle (mirrored below), and the eigenvector matrix
+// is kept transposed (V^T) so that its rotations update two contiguous rows.  A rotation is
+// skipped when the off-diagonal element is below kJacobiAbsTol times the largest input
+// element or negligible next to both diagonal entries (binary exponent at least 61 below
+// each); the iteration stops after a sweep without rotations or without two active rows
+// (at most kMaxSweeps sweeps).  A lives in shared memory for dim <= kJacobiSmemA, V^T too
+// for dim <= kJacobiSmemAV; larger matrices use global work space (2 dim^2 doubles).
 constexpr int kJacobiSmemA = 160;
 // A rotation is skipped when |a_pq| <= kJacobiAbsTol * max |a_ij| of the input: the
 // eigen-decomposition is then accurate to about that fraction of the largest element
