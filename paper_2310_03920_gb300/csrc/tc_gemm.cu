@@ -6,7 +6,7 @@
 // in FP32 after one rounding of a to FP32, see split()); a
 // product a*b is formed as hi*hi + hi*lo + lo*hi on the tensor cores with FP32
 // accumulation in tensor memory (TMEM); the FP32 tile is added to the FP64 output at the
-// end.  One CTA (4 warps) owns a 128 x 128 output tile:
+// end.  One CTA (8 warps) owns a 128 x 128 output tile:
 //   3-operand term, per 64-wide chunk c of K2:
 //     T  = op(P)[tile rows, :] X[:, c]        (tcgen05.mma, TMEM columns [0, 64))
 //     T  -> registers, times alpha, split, back to shared memory (A operand)
@@ -36,6 +36,9 @@ constexpr int kKc = 64;          // K chunk staged in shared memory
 constexpr int kTmemCols = 256;   // T at [0, 64), accumulator at [128, 256)
 constexpr int kTileBytes = kRows * kKc * 2;   // one bf16 [128 x 64] K-major tile
 constexpr uint32_t kWaitLimit = 1u << 26;
+// 8 warps: all stage operands (twice the loads in flight of 4 warps); TMEM is read by warp w
+// in lane quarter w % 4, the two warpgroups taking alternate 16-column chunks
+constexpr int kThreads = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -114,7 +117,7 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
   const int n = rows_tile * kw;
   const float sf = static_cast<float>(s);
   if (!trans) {
-    for (int e = tid; e < n; e += 128) {
+    for (int e = tid; e < n; e += kThreads) {
       int i = e / kw, k = e - i * kw;
       int r = r0 + i, c = c0 + k;
       const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(r) * ld + c]) : 0.f;
@@ -125,7 +128,7 @@ __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char*
       *reinterpret_cast<__nv_bfloat16*>(lo + o) = l;
     }
   } else {
-    for (int e = tid; e < n; e += 128) {
+    for (int e = tid; e < n; e += kThreads) {
       int k = e / rows_tile, i = e - k * rows_tile;
       int r = r0 + i, c = c0 + k;
       const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(c) * ld + r]) : 0.f;
@@ -174,11 +177,12 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   const uint32_t tmem_t = tmem, tmem_acc = tmem + 128;
-  const uint32_t lane_off = uint32_t(warp * 32) << 16;
+  const int quad = warp & 3, wg = warp >> 2;   // TMEM lane quarter, warpgroup
+  const uint32_t lane_off = uint32_t(quad * 32) << 16;
 
   // rows of the A operand beyond the output block stay zero for every term
   const int m_rows = min(kRows, o.M - r0);
-  for (int e = tid; e < kTileBytes / 16; e += 128) {
+  for (int e = tid; e < kTileBytes / 16; e += kThreads) {
     reinterpret_cast<uint4*>(a_hi)[e] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(a_lo)[e] = make_uint4(0, 0, 0, 0);
   }
@@ -240,10 +244,10 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
         }
         if (!ok) break;
         // T (FP32, row = thread) -> alpha * T split into the A operand
-        if (warp * 32 < m_rows) {   // warps holding only rows past the block: T is zero there
-          const int row = warp * 32 + lane;
+        if (quad * 32 < m_rows) {   // warps holding only rows past the block: T is zero there
+          const int row = quad * 32 + lane;
           const float af = static_cast<float>(g.alpha);
-          for (int cc = 0; cc < n_t; cc += 16) {
+          for (int cc = wg * 16; cc < n_t; cc += 32) {
             float v[16];
             tmem_ld16(tmem_t + lane_off + uint32_t(cc), v);
 #pragma unroll
@@ -266,9 +270,9 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
 
   if (ok) {
     double* out = bt.p[o.buf] + o.off;
-    const int row = warp * 32 + lane;
+    const int row = quad * 32 + lane;
     const int r = r0 + row;
-    for (int cc = 0; cc < n_acc; cc += 16) {
+    for (int cc = wg * 16; cc < n_acc; cc += 32) {
       float v[16];
       if (started) {
         tmem_ld16(tmem_acc + lane_off + uint32_t(cc), v);
@@ -297,7 +301,7 @@ __device__ __forceinline__ void gemm_tc_item(const GemmTile& tile, const GemmOut
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles,
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(const GemmTile* __restrict__ tiles,
                                                  const GemmOut* __restrict__ outs,
                                                  const GemmTerm* __restrict__ terms, BufTable bt,
                                                  int* status) {
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
 
 // Grouped launch over several problems: CTA b takes tile b - tile0 of the group g with
 // tile0(g) <= b < tile0(g + 1).
-__global__ void __launch_bounds__(128) k_gemm_tc_grouped(const GemmGroupTc* __restrict__ groups,
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_tc_grouped(const GemmGroupTc* __restrict__ groups,
                                                          int n_groups, int* status) {
   int lo = 0, hi = n_groups - 1;
   const int b = blockIdx.x;
@@ -328,7 +332,7 @@ void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, con
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gemm_tc_smem()));
   });
-  k_gemm_tc<<<n_tiles, 128, gemm_tc_smem(), s>>>(tiles, outs, terms, bt, status);
+  k_gemm_tc<<<n_tiles, kThreads, gemm_tc_smem(), s>>>(tiles, outs, terms, bt, status);
   count_launches(1);
 }
 
@@ -340,7 +344,7 @@ void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles
     cudaFuncSetAttribute(k_gemm_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(gemm_tc_smem()));
   });
-  k_gemm_tc_grouped<<<n_tiles, 128, gemm_tc_smem(), s>>>(groups, n_groups, status);
+  k_gemm_tc_grouped<<<n_tiles, kThreads, gemm_tc_smem(), s>>>(groups, n_groups, status);
   count_launches(1);
 }
 
