@@ -110,33 +110,41 @@ __device__ __forceinline__ void split(float f, __nv_bfloat16& hi, __nv_bfloat16&
 // Stage op(M)[r0 + i][c0 + k] (i < rows_tile, k < kw; zero outside rows x cols) as the
 // K-major operand (row i, K index k), scaled by s, into hi/lo tiles.  kw (a multiple of 16)
 // covers the K-steps the MMA will read; rows >= rows_tile are left as they are (zero).
+// Each thread loads kStageBatch elements before converting any of them, so that many L2 /
+// HBM loads are in flight per thread (the staging is bound by load latency).
+constexpr int kStageBatch = 4;
 __device__ __forceinline__ void stage_rowmajor(unsigned char* hi, unsigned char* lo, const double* M,
                                                int ld, int rows, int cols, int r0, int c0,
                                                bool trans, int rows_tile, int kw, double s,
                                                int tid) {
   const int n = rows_tile * kw;
   const float sf = static_cast<float>(s);
-  if (!trans) {
-    for (int e = tid; e < n; e += kThreads) {
-      int i = e / kw, k = e - i * kw;
-      int r = r0 + i, c = c0 + k;
-      const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(r) * ld + c]) : 0.f;
-      __nv_bfloat16 h, l;
-      split(x, h, l);
-      uint32_t o = koff(i, k);
-      *reinterpret_cast<__nv_bfloat16*>(hi + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(lo + o) = l;
+  for (int e0 = tid; e0 < n; e0 += kThreads * kStageBatch) {
+    double v[kStageBatch];
+    uint32_t off[kStageBatch];
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      int i = 0, k = 0;
+      if (!trans) {
+        i = e / kw;
+        k = e - i * kw;
+      } else {
+        k = e / rows_tile;
+        i = e - k * rows_tile;
+      }
+      const int r = r0 + i, c = c0 + k;
+      const bool in = e < n && r < rows && c < cols;
+      v[u] = in ? (trans ? M[int64_t(c) * ld + r] : M[int64_t(r) * ld + c]) : 0.0;
+      off[u] = e < n ? koff(i, k) : 0xffffffffu;
     }
-  } else {
-    for (int e = tid; e < n; e += kThreads) {
-      int k = e / rows_tile, i = e - k * rows_tile;
-      int r = r0 + i, c = c0 + k;
-      const float x = (r < rows && c < cols) ? sf * static_cast<float>(M[int64_t(c) * ld + r]) : 0.f;
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      if (off[u] == 0xffffffffu) continue;
       __nv_bfloat16 h, l;
-      split(x, h, l);
-      uint32_t o = koff(i, k);
-      *reinterpret_cast<__nv_bfloat16*>(hi + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(lo + o) = l;
+      split(sf * static_cast<float>(v[u]), h, l);
+      *reinterpret_cast<__nv_bfloat16*>(hi + off[u]) = h;
+      *reinterpret_cast<__nv_bfloat16*>(lo + off[u]) = l;
     }
   }
 }
