@@ -300,3 +300,21 @@ def test_random_mps_is_right_canonical_and_normalised():
         for (jl, s, jr) in blocks:
             ql, qr = bonds[k][jl], bonds[k + 1][jr]
             assert ql[0] + ops.SITE_Q[s][0] == qr[0] and ql[1] + ops.SITE_Q[s][1] == qr[1]
+
+
+def test_graded_density_matrices_have_the_stated_spectrum():
+    # the eigensolver benchmark's inputs: symmetric, positive semidefinite, eigenvalues
+    # 10^(-16 i/(r-1)) for i < r = floor(0.7 m) + 1 and zero beyond, and seeded
+    from synth import TRUNCATION_BATCH_DIMS, graded_density_matrices
+    dims = [1, 2, 17, 64]
+    mats = graded_density_matrices(dims, seed=5)
+    again = graded_density_matrices(dims, seed=5)
+    for m, a, b in zip(dims, mats, again):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, a.T)
+        r = int(0.7 * m) + 1
+        lam = np.zeros(m)
+        lam[:r] = 10.0 ** (-16.0 * np.arange(r) / max(r - 1, 1))
+        w = np.sort(np.linalg.eigvalsh(a))[::-1]
+        assert np.abs(w - lam).max() < 1e-14
+    assert len(TRUNCATION_BATCH_DIMS) == 43 and max(TRUNCATION_BATCH_DIMS) == 147
