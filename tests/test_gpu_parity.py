@@ -172,6 +172,45 @@ def test_eigh_batched_vs_numpy(ctx):
         vo += d * d
 
 
+def test_eigh_batched_edge_cases(ctx):
+    # zero, diagonal, identity, identity + rank one (a degenerate eigenvalue), scales near
+    # the ends of the FP64 range (the kernels scale by a power of two on entry), and graded
+    # density-matrix-like inputs; the one-CTA entry point must agree bitwise
+    from synth import graded_density_matrices
+    rng = np.random.default_rng(17)
+    mats = [np.zeros((5, 5)), np.diag(rng.standard_normal(9)), np.eye(70)]
+    u = rng.standard_normal(66)
+    mats.append(np.eye(66) + np.outer(u, u))
+    x = rng.standard_normal((40, 40))
+    mats.append(1e200 * (x + x.T))
+    mats.append(1e-200 * (x + x.T))
+    mats += graded_density_matrices([96, 31, 130], seed=9)
+    dims = [a.shape[0] for a in mats]
+    a_t = torch.tensor(np.concatenate([a.ravel() for a in mats]), device=DEV)
+    out = []
+    for fn in (b2.b2_eigh_batched, b2.b2_eigh_batched_static):
+        ev = torch.empty(sum(dims), dtype=torch.float64, device=DEV)
+        vec = torch.empty(sum(d * d for d in dims), dtype=torch.float64, device=DEV)
+        fn(ctx, dims, a_t, ev, vec)
+        torch.cuda.synchronize()
+        out.append((ev.cpu().numpy(), vec.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    ev, vec = out[0]
+    eo = vo = 0
+    for d, a in zip(dims, mats):
+        w = ev[eo:eo + d]
+        v = vec[vo:vo + d * d].reshape(d, d)
+        scale = max(np.abs(a).max(), np.finfo(float).tiny)
+        assert np.all(np.diff(w) <= 0)
+        assert np.abs(w - np.linalg.eigvalsh(a)[::-1]).max() <= 1e-13 * scale * d
+        assert np.abs(v.T @ v - np.eye(d)).max() <= 1e-13 * d
+        assert np.abs((a / scale) @ v - v * (w / scale)).max() <= 1e-13 * d
+        if not np.any(a - np.diag(np.diag(a))):   # diagonal input: nothing to rotate
+            assert np.array_equal(np.sort(w), np.sort(np.diag(a)))
+        eo += d
+        vo += d * d
+
+
 def _golden():
     with open(os.path.join(GOLDEN, "dmrg_oracle.json")) as f:
         return json.load(f)["cases"]
