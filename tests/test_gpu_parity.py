@@ -13,7 +13,7 @@ if not torch.cuda.is_available():
 
 from oracle import dmrg, mpo  # noqa: E402
 from paper_2310_03920_gb300 import b2  # noqa: E402
-from synth import (ab_initio_integrals, config_integrals, hubbard_integrals,  # noqa: E402
+from synth import (ab_initio_integrals, hubbard_integrals,  # noqa: E402
                    occupancies, random_mps, sector_sizes)
 from tests.helpers import dense_to_layout, layout_mask, layout_to_dense  # noqa: E402
 

@@ -7,7 +7,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import dmrg, fci, hamiltonian, mpo, ops
+from oracle import dmrg, fci, mpo, ops
 from synth import (ab_initio_integrals, hubbard_integrals, occupancies, random_mps,
                    sector_sizes)
 
