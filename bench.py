@@ -14,9 +14,10 @@ GEMMs the contraction performs, summed over every product in the sweep, divided 
 sweep's device time).  e2e: the same metric when each step also imports the MPS from host
 memory, builds the environments and exports the MPS back (host copies inside the timed
 region).  roofline: the kernel with the larger device time in the timed sweeps -- the
-H_eff contraction (algorithmic block-GEMM flops) or the truncation eigensolver (18 m flops
-per applied Jacobi rotation) -- timed by CUDA events inside the library, against the FP64
-peak measured on this GPU with cuBLAS DGEMM; roofline_other: the other one.
+H_eff contraction (algorithmic block-GEMM flops) or the truncation eigensolver (12 m_a + 6 m
+flops per applied Jacobi rotation, m_a the rows active in that sweep) -- timed by CUDA
+events inside the library, against the FP64 peak measured on this GPU with cuBLAS DGEMM;
+roofline_other: the other one.
 
 ``--impl reference`` times the CPU oracle (``oracle/``) on a bounded sample of the same
 workload (H_eff . psi products at the middle window) on the host cores.
@@ -504,7 +505,7 @@ def run_eig(args):
     """The truncation eigensolver alone (b2_eigh_batched): one batch shaped like a
     truncation step of the Hubbard L = 32, M = 500 sweep (43 sectors, dims 147 .. 2) of
     graded density-matrix-like matrices (synth.graded_density_matrices, seed 5).  value =
-    applied-rotation flops (18 m per rotation) / device time of the batched call."""
+    applied-rotation flops (12 m_active + 6 m per rotation) / device time of the batched call."""
     import numpy as np
     import torch
     from paper_2310_03920_gb300 import b2
@@ -537,7 +538,7 @@ def run_eig(args):
             "config": {"workload": "truncation_batch43_graded_density_matrices", "dims": dims,
                        "spectrum": "10^(-16 i/(r-1)), r = 0.7 m + 1, zero beyond",
                        "l2": "inputs resident (~1.2 MB); the kernel works in L2"},
-            "roofline": {"kernel": "k_jacobi + k_jacobi_cluster (18 m flops per applied rotation)",
+            "roofline": {"kernel": "k_jacobi + k_jacobi_cluster (12 m_active + 6 m flops per applied rotation)",
                          "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak if peak else None,
                          "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64)",
@@ -684,7 +685,7 @@ def main():
     rl_heff = fp64_roofline("k_gemm (H_eff block contraction, FP64)", prof["heff_flops"],
                             prof["heff_ms"], prof["heff_launches"])
     rl_eig = fp64_roofline("k_jacobi + k_jacobi_cluster (truncation eigensolver, FP64; "
-                           "18 m flops per applied rotation of an m x m block)",
+                           "12 m_active + 6 m flops per applied rotation of an m x m block)",
                            prof["eig_flops"], prof["eig_ms"], prof["eig_launches"])
     if prof["eig_ms"] > prof["heff_ms"]:
         roofline, roofline_other = rl_eig, rl_heff

@@ -308,7 +308,8 @@ typedef struct {
   double heff_flops;       /* their summed algorithmic flops */
   int64_t eig_launches;    /* truncation eigensolver calls timed (a kernel per cluster size) */
   double eig_ms;           /* their summed device time */
-  double eig_flops;        /* 18 m flops per applied Jacobi rotation of an m x m block */
+  double eig_flops;        /* 12 m_a + 6 m flops per applied Jacobi rotation of an m x m block
+                              (m_a: rows active in that sweep) */
   int64_t rr_launches;     /* Davidson Rayleigh-Ritz eigensolves timed (k x k, one CTA) */
   double rr_ms;            /* their summed device time */
 } b2_profile_data;

@@ -308,9 +308,10 @@ constexpr int kJacobiSmemA = 160;
 // matrices, whose smallest eigenvalues are rounding noise, stop after about 10 to 30
 // sweeps (dims 16 to 300) instead of chasing that noise up to kMaxSweeps.
 constexpr double kJacobiAbsTol = 1e-15;
-// Algorithmic flops of one applied rotation of an m x m problem (textbook count: the two
-// rows and two columns of A, 12 m, and two columns of V, 6 m), for the profiling counter.
-constexpr double kJacobiRotFlops = 18.0;
+// Algorithmic flops of one applied rotation in a sweep over ms active rows of an m x m
+// problem (textbook count: the two rows and two columns of A within the active rows,
+// 12 ms, and two columns of V, 6 m), for the profiling counter.
+constexpr double kJacobiRotFlopsA = 12.0, kJacobiRotFlopsV = 6.0;
 constexpr int kMaxSweeps = 60;
 constexpr int kJacobiThreads = 512;
 
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
   extern __shared__ double smem[];
   __shared__ int nact[2];    // rotating pairs of the round (double-buffered by round parity)
   __shared__ int nrot;       // rotations applied in the sweep
-  long long rot_total = 0;   // thread 0: rotations applied
+  double rot_flops = 0.0;    // thread 0: flops of the rotations applied
   const int b = ids ? ids[blockIdx.x] : int(blockIdx.x), tid = threadIdx.x, nt = blockDim.x;
   const int m = dims[b];
   const int mp = m + (m & 1), half = mp / 2;
@@ -601,11 +602,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
       }
       __syncthreads();
     }
-    if (tid == 0) rot_total += nrot;
+    if (tid == 0) rot_flops += double(nrot) * (kJacobiRotFlopsA * ms + kJacobiRotFlopsV * m);
     if (nrot == 0) break;
     __syncthreads();   // every thread has read nrot before it is reset
   }
-  if (flop_counter && tid == 0) atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
+  if (flop_counter && tid == 0) atomicAdd(flop_counter, rot_flops);
   // descending order, ties by index
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   };
   __shared__ int nact[2];
   __shared__ int nrot;
-  long long rot_total = 0;   // thread 0: rotations applied
+  double rot_flops = 0.0;    // thread 0: flops of the rotations applied
   const double* src = a + offs[b];
   const int gt = crank * nt + tid, gn = C * nt;
   if (tid == 0) nact[0] = nact[1] = 0;
@@ -893,12 +894,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
       cluster_wait_acquire();
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
-    if (tid == 0) rot_total += nrot;
+    if (tid == 0) rot_flops += double(nrot) * (kJacobiRotFlopsA * ms + kJacobiRotFlopsV * m);
     if (nrot == 0) break;
     __syncthreads();   // every thread has read nrot before it is reset
   }
-  if (flop_counter && crank == 0 && tid == 0)
-    atomicAdd(flop_counter, kJacobiRotFlops * m * double(rot_total));
+  if (flop_counter && crank == 0 && tid == 0) atomicAdd(flop_counter, rot_flops);
   // descending order, ties by index; every CTA ranks all rows and writes its own columns
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];

@@ -141,7 +141,7 @@ inline bool jacobi_needs_work(int dim, int csize) { return csize > 1 || dim > kJ
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s,
-                   double* flop_counter = nullptr);   // += 18 m per applied rotation
+                   double* flop_counter = nullptr);   // += 12 m_active + 6 m per rotation
 // Host-side plan of a batch: a cluster size per matrix and the matrices grouped by size
 // (ids, class by class).  GB300 runs FP64 at ~1.75 FMA per clock per SM, so one CTA is
 // arithmetic-bound on a large matrix; the plan starts from one CTA per matrix and keeps
