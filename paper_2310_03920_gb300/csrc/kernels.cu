@@ -625,15 +625,20 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
 
 // The same rotation sequence for one matrix spread over a cluster of CTAs: GB300's FP64
 // rate per SM is low (about 1.75 operations per clock), so one SM per large matrix bounds the
-// whole truncation.  A and V^T stay in the global work space (L2 resident).  Every round,
+// whole truncation.  A is distributed over the cluster's shared memory by rows (row x in CTA
+// x mod C) where it fits, else it stays in the global work space (L2 resident); V^T is split
+// in column slices, one per CTA (shared memory where it fits).  Each sweep first marks the
+// active rows (deflation: rows with an off-diagonal element above the threshold; every CTA
+// checks its rows and writes the flags into all CTAs) and pairs only those.  Every round,
 // each CTA computes all the round's rotations from its own copy of the round's pivots
 // (diagonal entries and pair off-diagonals, identical in every CTA); the 2 x 2 blocks of A
-// are dealt out round-robin over the CTAs (block e to CTA e mod C) and the columns of V^T in
-// contiguous slices, so every CTA carries 1/C of the round's FP64 work; the thread that
-// writes a pivot element of the NEXT round also writes it into every CTA's pivot copy
-// (double-buffered by round parity); one cluster barrier per round then orders everything.
-// Each element sees the same operations in the same order as in k_jacobi, so the results
-// are identical.  One cluster per matrix: cluster k of the grid solves matrix ids[k].
+// are dealt out round-robin over the CTAs (block e to CTA e mod C), so every CTA carries
+// 1/C of the round's FP64 work; the thread that writes a pivot element of the NEXT round
+// also writes it into every CTA's pivot copy (double-buffered by round parity); one cluster
+// barrier per round then orders everything, and the CTA's own V^T slice is rotated between
+// its arrive and wait.  Each element sees the same operations in the same order as in
+// k_jacobi, so the results are identical.  One cluster per matrix: cluster k of the grid
+// solves matrix ids[k].
 // barrier.cluster.arrive (release) + barrier.cluster.wait (acquire): orders the global
 // and distributed-shared-memory accesses of the cluster's threads around the barrier
 __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cl) { cl.sync(); }
