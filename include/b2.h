@@ -3,12 +3,12 @@
  *
  * The method is ab initio two-site DMRG as described in the block2 paper (arXiv
  * 2310.03920): an MPO for the Hamiltonian built from the integrals h_pq and (pq|rs)
- * (Sec. 2.3), renormalized operators (environments) on both sides of a two-site window
- * (Sec. 2.1.2 and Sec. 2.3, "renormalized operator view"), the effective Hamiltonian
- * H_eff acting on the two-site wavefunction inside a Davidson eigensolver (Sec. 2.1.3
- * (iv) "standard Davidson solver"; Listing 1: thrds, dav_max_iter), truncation of each
- * bond to M states, and the sweep (Sec. 2.1.2).  Symmetry: particle number and projected
- * spin, U(1) x U(1) ("SZ", Sec. 2.1.1).
+ * (Sec. 2.3), environments (the operators of the blocks left and right of a two-site
+ * window, Sec. 2.1.2 and Sec. 2.3), the effective Hamiltonian H_eff acting on the
+ * two-site wavefunction inside a Davidson eigensolver (Sec. 2.1.3 (iv); Listing 1 for the
+ * thrds and dav_max_iter settings), truncation of each bond to M states, and the sweep
+ * (Sec. 2.1.2).  Symmetry: particle number and projected spin, U(1) x U(1) (the SZ mode
+ * of Sec. 2.1.1).
  *
  * Conventions shared by every call
  *   - Local site basis [|0>, |alpha>, |beta>, |alpha beta>] with (N, 2Sz) = (0,0), (1,1),
@@ -90,7 +90,7 @@ const char* b2_last_error(b2_ctx ctx);
  * operator strings (Sec. 2.3): operators with at most two elementary operators on the
  * left of a bond are normal operators, the rest are carried as complementary operators,
  * and the partition switches from normal/complementary to complementary/normal after
- * the middle site (Sec. 2.3, "Symbolic MPO approach").
+ * the middle site (the symbolic MPO construction of Sec. 2.3).
  *   h1   host, n_orb x n_orb row-major, h1[p*n+q] = h_pq (symmetric)
  *   eri  host, n_orb^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs)
  *   integrals with |value| <= cutoff are dropped (0 keeps every nonzero)
@@ -257,19 +257,20 @@ int b2_eigh_batched(b2_ctx ctx, int n_mat, const int* dims, const double* a, dou
 
 /* Same eigensolver, for callers that cannot allocate device memory.  (The paper has no
  * counterpart; this is an interface for embedding.)  Some callers must not let a library
- * allocate: code running while a CUDA stream is being captured into a graph (allocation
- * calls are illegal then), runtimes that own all device memory through their own pool
- * and forbid other allocators, and latency-critical loops where an allocation could
- * block on the device.  This variant calls no cudaMalloc, cudaFree or allocating library
- * routine: its scratch -- the per-matrix sizes and offsets and the global-memory work
- * space of matrices with dim > 112 -- lives in a fixed device array inside the library,
- * 4 MiB + 32 KiB, which every GPU that loads the library holds until the process exits.
- * The caller still passes the inputs and outputs (same layout as b2_eigh_batched).
+ * allocate: runtimes that own all device memory through their own pool and forbid other
+ * allocators, and latency-critical loops where an allocation could synchronise with the
+ * device or fail under memory pressure.  This variant calls no cudaMalloc, cudaFree or
+ * allocating library routine: its scratch -- the per-matrix sizes and offsets and the
+ * global-memory work space of matrices with dim > 112 -- lives in a fixed device array
+ * inside the library, 4 MiB + 32 KiB, which every GPU that loads the library holds until
+ * the process exits.  The caller still passes the inputs and outputs (same layout as
+ * b2_eigh_batched); the sizes reach the device as a kernel argument.
  *   Limits: n_mat <= 1024; dims in [1, 1024]; the matrices with dim > 112 together need
  *   2 * dim^2 doubles of work space, at most 524288 doubles.  Larger requests return
  *   B2_EINVAL without touching the device.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress
- *   with that device current); make that first call before any stream capture.
+ *   with that device current) and keeps it for the life of the process; make that first
+ *   call before any stream capture, and do not reset the device in between.
  *   All calls share the array and it keeps the last call's contents; calls whose work
  *   overlaps on the GPU (e.g. on two streams at once) race on it.  The call is
  *   stream-ordered and returns without waiting for the result. */
@@ -315,6 +316,16 @@ typedef struct {
 } b2_profile_data;
 int b2_profile(b2_ctx ctx, int enable);
 int b2_profile_read(b2_ctx ctx, b2_profile_data* out);
+
+/* --------------------------------------------------------------------- test support
+ * Shorter device-side limits for tests of the failure paths (no counterpart in the
+ * paper): tests make a limit run out on purpose and check the status that comes back,
+ * without faulting or hanging anything.  wait_iters: polls of a bounded device wait in the
+ * tensor-core contraction before it gives up (0 = the built-in limit, about a second or
+ * more) -- a call whose wait ran out returns B2_ETIMEOUT and the context stays usable;
+ * jacobi_max_sweeps: sweeps of the truncation eigensolver before b2_sweep reports
+ * B2_ENOCONV for a sector still rotating (0 = the built-in 60).  Per context. */
+int b2_debug_limits(b2_ctx ctx, int wait_iters, int jacobi_max_sweeps);
 
 void b2_free_mpo(b2_mpo mpo);
 void b2_free_mps(b2_mps mps);

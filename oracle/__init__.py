@@ -9,8 +9,8 @@ follows):
   ops          local Fock basis and elementary operators (Listing 1, Part A)
   hamiltonian  ab initio Hamiltonian as a list of site-ordered operator strings (Sec. 2.1.1)
   fci          determinant full CI, first-quantised two-electron check, Hubbard-Holstein FCI
-  mpo          exact MPO from the operator strings: a prefix tree (Sec. 2.3 "General MPO
-               construction")
+  mpo          exact MPO from the operator strings: a prefix tree (the general MPO
+               construction of Sec. 2.3)
   dmrg         environments, effective Hamiltonian, Davidson, truncation and the two-site
                sweep (Sec. 2.1.2)
   rdm          one- and two-particle density matrices (Sec. 2.5.1)

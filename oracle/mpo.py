@@ -4,7 +4,7 @@ The paper builds MPOs automatically from a symbolic list of operator strings (Se
 "General MPO construction for Hamiltonians") and, for ab initio Hamiltonians, arranges
 the renormalized operators into normal and complementary sets, switching from the
 normal/complementary (NC) to the complementary/normal (CN) partition at the middle site
-(Sec. 2.3, "Symbolic MPO approach").  Two constructions are written here:
+(the symbolic MPO construction of Sec. 2.3).  Two constructions are written here:
 
 ``kind="trie"``  the plainest exact MPO: the channels on bond k (between sites k-1 and k)
     are "I" (nothing of the term applied yet), "H" (term complete) and the prefix (the

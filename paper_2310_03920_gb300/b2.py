@@ -76,6 +76,7 @@ _sig = {
     "b2_heff_apply_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_d)]),
     "b2_davidson_batched": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(DavOpts), _vp, _vp, _vp]),
     "b2_sweep_batched": (_i, [_vp, _i, _vp, ctypes.POINTER(SweepOpts), _vp]),
+    "b2_debug_limits": (_i, [_vp, _i, _i]),
     "b2_profile": (_i, [_vp, _i]),
     "b2_profile_read": (_i, [_vp, ctypes.POINTER(ProfileData)]),
     "b2_free_mpo": (None, [_vp]),
@@ -109,20 +110,31 @@ def _ptr(t):
 
 
 class Context:
-    """A libb2 context on a CUDA device and stream, with torch's caching allocator."""
+    """A libb2 context on a CUDA device and stream.  Device memory comes from torch's
+    caching allocator, or from the given alloc(size) -> pointer (0 = failure) and free(ptr)
+    callables."""
 
-    def __init__(self, device=0, stream=None):
+    def __init__(self, device=0, stream=None, alloc=None, free=None):
         import torch
         self.torch = torch
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         dev, st = device, self.stream
+        if (alloc is None) != (free is None):
+            raise ValueError("give both alloc and free, or neither")
 
-        def _alloc(size, user):
-            return torch.cuda.caching_allocator_alloc(int(size), dev, st)
+        if alloc is None:
+            def _alloc(size, user):
+                return torch.cuda.caching_allocator_alloc(int(size), dev, st)
 
-        def _free(p, user):
-            torch.cuda.caching_allocator_delete(p)
+            def _free(p, user):
+                torch.cuda.caching_allocator_delete(p)
+        else:
+            def _alloc(size, user):
+                return alloc(int(size)) or None
+
+            def _free(p, user):
+                free(p)
 
         self._cb = (_ALLOC(_alloc), _FREE(_free))
         h = _vp()
@@ -334,6 +346,10 @@ def b2_rdm_grad(ctx, mpo, mps, n):
     g2 = np.zeros((n, n, n, n), dtype=np.float64)
     _check(ctx.h, lib.b2_rdm_grad(ctx.h, mpo, mps, g1.ctypes.data, g2.ctypes.data))
     return g1, g2
+
+
+def b2_debug_limits(ctx, wait_iters=0, jacobi_max_sweeps=0):
+    _check(ctx.h, lib.b2_debug_limits(ctx.h, wait_iters, jacobi_max_sweeps))
 
 
 def b2_profile(ctx, enable=True):

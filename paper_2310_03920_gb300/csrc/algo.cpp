@@ -46,7 +46,7 @@ struct Tracer {
 
 void eigh_batched(Ctx* c, const std::vector<int>& dims, const std::vector<int64_t>& offs,
                   const std::vector<int64_t>& eoffs, const double* a, double* evals,
-                  double* evecs, double* flop_counter) {
+                  double* evecs, double* flop_counter, int* unconverged) {
   const int n = int(dims.size());
   if (n == 0) return;
   const b2k::JacobiPlan plan = b2k::plan_jacobi(dims);
@@ -74,7 +74,8 @@ void eigh_batched(Ctx* c, const std::vector<int>& dims, const std::vector<int64_
   side.fork = c->side_fork;
   b2k::launch_jacobi_plan(plan, d_ids.as<int>(), d_dims.as<int>(), d_offs.as<int64_t>(),
                           d_eoffs.as<int64_t>(), a, evals, evecs, work.as<double>(),
-                          d_woffs.as<int64_t>(), c->stream, &side, flop_counter);
+                          d_woffs.as<int64_t>(), c->stream, &side,
+                          b2k::JacobiCtl{flop_counter, unconverged, c->jacobi_max_sweeps});
   B2_CUDA(cudaGetLastError());
 }
 
@@ -348,8 +349,9 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     B2_CUDA(cudaEventCreate(&e1));
     B2_CUDA(cudaEventRecord(e0, c->stream));
   }
+  int* unconv = c->status() + 1;   // status word 1: Jacobi sweep limit reached
   eigh_batched(c, dims, offs, eoffs, rho.as<double>(), evals.as<double>(), evecs.as<double>(),
-               c->prof ? c->d_eig_flops : nullptr);
+               c->prof ? c->d_eig_flops : nullptr, unconv);
   if (c->prof) {
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->eig_events.push_back({e0, e1});
@@ -359,9 +361,17 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
   B2_CUDA(cudaGetLastError());
   std::vector<int> kept(ns);
   double w[2];
+  int n_unconv = 0;
   B2_CUDA(cudaMemcpyAsync(kept.data(), d_kept.ptr, sizeof(int) * ns, cudaMemcpyDeviceToHost, c->stream));
   B2_CUDA(cudaMemcpyAsync(w, d_w.ptr, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  B2_CUDA(cudaMemcpyAsync(&n_unconv, unconv, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sync(c);
+  if (n_unconv != 0) {
+    B2_CUDA(cudaMemsetAsync(unconv, 0, sizeof(int), c->stream));
+    B2_REQUIRE(false, B2_ENOCONV,
+               "density-matrix eigensolver: " + std::to_string(n_unconv) +
+                   " sector(s) still rotating after the sweep limit");
+  }
   *discarded = w[0];
   return kept;
 }

@@ -14,10 +14,12 @@ struct DavidsonResult {
 // each, row-major): eigenvalues in descending order to evals + eoffs[j], eigenvectors as the
 // columns of evecs + offs[j].  Plans a cluster size per matrix (b2k::plan_jacobi), allocates
 // the work space and runs the size classes concurrently on the context's side streams.
-// Stream-ordered on c->stream; flop_counter: optional device counter of applied rotations.
+// Stream-ordered on c->stream; flop_counter: optional device counter of applied rotations;
+// unconverged: optional device counter of matrices that used up the sweep limit
+// (c->jacobi_max_sweeps, 0 = the default).
 void eigh_batched(Ctx* c, const std::vector<int>& dims, const std::vector<int64_t>& offs,
                   const std::vector<int64_t>& eoffs, const double* a, double* evals,
-                  double* evecs, double* flop_counter = nullptr);
+                  double* evecs, double* flop_counter = nullptr, int* unconverged = nullptr);
 void contract_two_sites(Ctx* c, const Bond& ba, const Bond& bb, const SiteTensor& X,
                         const double* xd, const SiteTensor& Y, const double* yd,
                         const PsiLayout& lay, double* out, double* flops);

@@ -374,6 +374,15 @@ int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri
   });
 }
 
+int b2_debug_limits(b2_ctx ctx, int wait_iters, int jacobi_max_sweeps) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(ctx, B2_EINVAL, "null context");
+    B2_REQUIRE(wait_iters >= 0 && jacobi_max_sweeps >= 0, B2_EINVAL, "limits must be >= 0");
+    ctx->c.wait_limit = uint32_t(wait_iters);
+    ctx->c.jacobi_max_sweeps = jacobi_max_sweeps;
+  });
+}
+
 int b2_profile(b2_ctx ctx, int enable) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx, B2_EINVAL, "null context");

@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 
 namespace b2 {
@@ -610,6 +612,28 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
       t.alpha = p.coef * sign;
       prog.add_term(ob, t);
     }
+  }
+  if (std::getenv("B2_TRACE_WINDOW")) {
+    // structure of the contraction: term shapes (rows m_l', K1 = m_l, K2 = m_r, cols m_r')
+    // weighted by their flops, and the 128-row / 64-wide padding of the tensor-core tiles
+    double fl = 0, fl_pad = 0, n_terms = 0;
+    std::map<int, double> by_rows;   // flops by rows of the output block (bucketed)
+    for (size_t o = 0; o < prog.outs.size(); ++o) {
+      const auto& out = prog.outs[o];
+      for (const auto& t : prog.by_out[o]) {
+        const double f = 2.0 * out.M * t.K1 * t.K2 + 2.0 * out.M * double(t.K2) * out.N;
+        fl += f;
+        n_terms += 1;
+        const double mp = 128.0 * ((out.M + 127) / 128), k1 = 16.0 * ((t.K1 + 15) / 16),
+                     k2 = 16.0 * ((t.K2 + 15) / 16), np_ = 16.0 * ((out.N + 15) / 16);
+        fl_pad += 2.0 * mp * k1 * k2 + 2.0 * mp * k2 * np_;
+        by_rows[out.M <= 16 ? 16 : out.M <= 32 ? 32 : out.M <= 64 ? 64 : out.M <= 128 ? 128 : 256] += f;
+      }
+    }
+    std::fprintf(stderr, "window %d: outs %zu terms %.0f flops %.4g padded128 %.4g L %lld R %lld comb %lld psi %lld\n",
+                 i, prog.outs.size(), n_terms, fl, fl_pad, (long long)L.size, (long long)R.size,
+                 (long long)(combL.size + combR.size), (long long)wp.psi.size);
+    for (auto& kv : by_rows) std::fprintf(stderr, "  rows<=%d: %.3f of flops\n", kv.first, kv.second / fl);
   }
   prog.finalize(c, true);   // FP64 and tensor-core tilings
   int64_t comb_size = combL.size + combR.size;

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
                                                            double* work,
                                                            const int64_t* __restrict__ woffs,
                                                            const int* __restrict__ ids,
-                                                           double* flop_counter) {
+                                                           JacobiCtl ctl) {
   extern __shared__ double smem[];
   __shared__ int nact[2];    // rotating pairs of the round (double-buffered by round parity)
   __shared__ int nrot;       // rotations applied in the sweep
@@ -522,12 +522,17 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
   const long long tol_bits = __double_as_longlong(kJacobiAbsTol * (amax * sc));
   __syncthreads();
   int gr = 0;                               // rounds so far, over all sweeps
-  for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
+  const int max_sweeps = ctl.max_sweeps > 0 ? ctl.max_sweeps : kMaxSweeps;
+  bool done = m <= 1;                       // stopped by the threshold, not the sweep limit
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
     // the sweep pairs the active rows only (round-robin over their positions in sidx)
     for (int x = tid; x < m; x += nt) uc[x] = jacobi_row_active(A + x * m, x, m, tol_bits);
     __syncthreads();
     const int ms = block_compact(uc, m, sidx, spos, wsum);
-    if (ms < 2) break;
+    if (ms < 2) {
+      done = true;
+      break;
+    }
     const int msp = ms + (ms & 1), hs = msp / 2;
     const int nblk = hs * (hs + 1) / 2;   // upper-triangle 2x2 blocks (i <= j) of the pairs
     if (tid == 0) nrot = 0;
@@ -603,10 +608,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(const int* __restrict
       __syncthreads();
     }
     if (tid == 0) rot_flops += double(nrot) * (kJacobiRotFlopsA * ms + kJacobiRotFlopsV * m);
-    if (nrot == 0) break;
+    if (nrot == 0) {
+      done = true;
+      break;
+    }
     __syncthreads();   // every thread has read nrot before it is reset
   }
-  if (flop_counter && tid == 0) atomicAdd(flop_counter, rot_flops);
+  if (ctl.flop_counter && tid == 0) atomicAdd(ctl.flop_counter, rot_flops);
+  if (!done && ctl.unconverged && tid == 0) atomicAdd(ctl.unconverged, 1);
   // descending order, ties by index
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
@@ -687,7 +696,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     const int* __restrict__ dims, const int64_t* __restrict__ offs,
     const int64_t* __restrict__ eoffs, const double* __restrict__ a, double* evals,
     double* evecs, double* work, const int64_t* __restrict__ woffs,
-    const int* __restrict__ ids, double* flop_counter) {
+    const int* __restrict__ ids, JacobiCtl ctl) {
   extern __shared__ double smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int C = int(cl.num_blocks());
@@ -765,7 +774,9 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
   };
   auto is_pivot = [&](int x, int y) { return x == y || partner[x] == y; };
   int gr = 0;   // rounds so far, over all sweeps
-  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+  const int max_sweeps = ctl.max_sweeps > 0 ? ctl.max_sweeps : kMaxSweeps;
+  bool done = false;   // stopped by the threshold (uniform over the cluster)
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // active rows (deflation): this CTA checks rows crank, crank + C, ... and writes the
     // flags into every CTA; all CTAs then hold the same flags and build the same list
     for (int x = crank + C * tid; x < m; x += C * nt) {
@@ -775,7 +786,10 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     }
     cluster_barrier(cl);
     const int ms = block_compact(uc, m, sidx, spos, wsum);
-    if (ms < 2) break;   // uniform: the same flags in every CTA
+    if (ms < 2) {   // uniform: the same flags in every CTA
+      done = true;
+      break;
+    }
     const int msp = ms + (ms & 1), hs = msp / 2;
     const int nblk = hs * (hs + 1) / 2;
     // pivots of the sweep's first round from A, in every CTA
@@ -900,10 +914,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_cluster(
     }
     // the count is the same in every CTA (same rotations), so the exit is uniform
     if (tid == 0) rot_flops += double(nrot) * (kJacobiRotFlopsA * ms + kJacobiRotFlopsV * m);
-    if (nrot == 0) break;
+    if (nrot == 0) {
+      done = true;
+      break;
+    }
     __syncthreads();   // every thread has read nrot before it is reset
   }
-  if (flop_counter && crank == 0 && tid == 0) atomicAdd(flop_counter, rot_flops);
+  if (ctl.flop_counter && crank == 0 && tid == 0) atomicAdd(ctl.flop_counter, rot_flops);
+  if (!done && ctl.unconverged && crank == 0 && tid == 0) atomicAdd(ctl.unconverged, 1);
   // descending order, ties by index; every CTA ranks all rows and writes its own columns
   double* ev = evals + eoffs[b];
   double* vec = evecs + offs[b];
@@ -984,7 +1002,7 @@ static int jacobi_max_cluster() {
 
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
-                   const int64_t* woffs, int max_dim, cudaStream_t s, double* flop_counter) {
+                   const int64_t* woffs, int max_dim, cudaStream_t s, const JacobiCtl& ctl) {
   if (n_mat <= 0) return;
   jacobi_max_cluster();   // sets the shared memory limits
   // the need is not monotonic in the dimension (V^T leaves shared memory above
@@ -992,7 +1010,7 @@ void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_
   size_t smem = 0;
   for (int m = 1; m <= max_dim; ++m) smem = std::max(smem, jacobi_smem_bytes(m));
   k_jacobi<<<n_mat, kJacobiThreads, smem, s>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
-                                               nullptr, flop_counter);
+                                               nullptr, ctl);
   g_launches += 1;
 }
 
@@ -1062,7 +1080,7 @@ JacobiPlan plan_jacobi(const std::vector<int>& dims) {
 void launch_jacobi_plan(const JacobiPlan& p, const int* ids, const int* dims, const int64_t* offs,
                         const int64_t* eoffs, const double* a, double* evals, double* evecs,
                         double* work, const int64_t* woffs, cudaStream_t s,
-                        const JacobiStreams* side, double* flop_counter) {
+                        const JacobiStreams* side, const JacobiCtl& ctl) {
   if (p.n_cls == 0) return;
   jacobi_max_cluster();
   // With side streams, class 0 (the largest clusters) runs on side stream 0, which has the
@@ -1083,7 +1101,7 @@ void launch_jacobi_plan(const JacobiPlan& p, const int* ids, const int* dims, co
     const size_t smem = p.cls_smem[k];
     if (C == 1) {
       k_jacobi<<<cnt, kJacobiThreads, smem, sk>>>(dims, offs, eoffs, a, evals, evecs, work, woffs,
-                                                  cids, flop_counter);
+                                                  cids, ctl);
     } else {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(unsigned(cnt) * unsigned(C), 1, 1);
@@ -1098,7 +1116,7 @@ void launch_jacobi_plan(const JacobiPlan& p, const int* ids, const int* dims, co
       cfg.attrs = attr_c;
       cfg.numAttrs = 1;
       cudaLaunchKernelEx(&cfg, k_jacobi_cluster, dims, offs, eoffs, a, evals, evecs, work, woffs,
-                         cids, flop_counter);
+                         cids, ctl);
     }
     g_launches += 1;
   }

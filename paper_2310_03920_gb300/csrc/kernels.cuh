@@ -137,11 +137,19 @@ void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStr
 // identical (bitwise) whichever size solves a matrix.
 constexpr int kJacobiSmemAV = 112;
 inline bool jacobi_needs_work(int dim, int csize) { return csize > 1 || dim > kJacobiSmemAV; }
+// Optional controls of a launch: flop_counter (device) += 12 m_active + 6 m per applied
+// rotation; unconverged (device) += 1 for every matrix that used up max_sweeps sweeps
+// (0 = the default of 60) with rotations still above the threshold.
+struct JacobiCtl {
+  double* flop_counter = nullptr;
+  int* unconverged = nullptr;
+  int max_sweeps = 0;
+};
 // One CTA per matrix, on stream s.
 void launch_jacobi(int n_mat, const int* dims, const int64_t* offs, const int64_t* eoffs,
                    const double* a, double* evals, double* evecs, double* work,
                    const int64_t* woffs, int max_dim, cudaStream_t s,
-                   double* flop_counter = nullptr);   // += 12 m_active + 6 m per rotation
+                   const JacobiCtl& ctl = JacobiCtl());
 // Host-side plan of a batch: a cluster size per matrix and the matrices grouped by size
 // (ids, class by class).  GB300 runs FP64 at ~1.75 FMA per clock per SM, so one CTA is
 // arithmetic-bound on a large matrix; the plan starts from one CTA per matrix and keeps
@@ -172,7 +180,7 @@ void launch_jacobi_plan(const JacobiPlan& plan, const int* ids, const int* dims,
                         const int64_t* offs, const int64_t* eoffs, const double* a,
                         double* evals, double* evecs, double* work, const int64_t* woffs,
                         cudaStream_t s, const JacobiStreams* side = nullptr,
-                        double* flop_counter = nullptr);
+                        const JacobiCtl& ctl = JacobiCtl());
 // Global top-M selection over n eigenvalues (sector-major, descending in each sector).
 // sector[i], index[i]: sector id and position in sector of value i.  Writes kept[sector]
 // (counts, zeroed first, n_sec entries) and out[0] = discarded weight, out[1] = kept weight.

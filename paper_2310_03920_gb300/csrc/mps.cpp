@@ -33,7 +33,7 @@ void Ctx::raw_free(void* p) {
 int* Ctx::status() {
   if (!d_status) {
     d_status = static_cast<int*>(raw_alloc(256));
-    B2_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+    B2_CUDA(cudaMemsetAsync(d_status, 0, 256, stream));
   }
   return d_status;
 }

@@ -6,7 +6,12 @@
 // holds it (kScratchBytes) until the process exits.  Host code cannot use the array's name
 // as a device address: the address is looked up once per device with
 // cudaGetSymbolAddress (on the first call made on that device, with the device current)
-// and passed to the kernel.  All calls share the array and it keeps the last call's
+// and passed to the kernels.  The cached address belongs to the device's primary context;
+// a cudaDeviceReset tears that context down and is not supported between calls.
+//
+// The matrix sizes reach the device as a kernel argument (by value), and a one-block
+// kernel writes the offsets into the array, so nothing is staged through host memory
+// that outlives the call.  All calls share the array and it keeps the last call's
 // contents; nothing in it has to start at zero (every call writes its metadata, and the
 // eigensolver initialises its work space).  Calls whose work overlaps on the GPU (for
 // example on two streams at once) race on the array.
@@ -41,14 +46,36 @@ double* scratch_address(int device) {
   return static_cast<double*>(g_address[device]);
 }
 
-// host staging of the metadata, reused by every call on this thread
+// Layout of the metadata region at the start of the array.
 struct Meta {
   int dims[kMaxMats];
   int pad[kMaxMats];   // keeps the int64 tables 8-byte aligned at a fixed offset
   int64_t offs[kMaxMats], eoffs[kMaxMats], woffs[kMaxMats];
 };
 static_assert(sizeof(Meta) <= kMetaDoubles * sizeof(double), "metadata exceeds its region");
-thread_local Meta t_meta;
+
+// The sizes of one call, passed by value (2 KiB of kernel arguments).
+struct Dims {
+  int n;
+  uint16_t d[kMaxMats];
+};
+
+// One thread writes the sizes and the prefix sums of dim^2 (matrices and eigenvectors),
+// dim (eigenvalues) and 2 dim^2 over the matrices with dim > kShmemDim (work space).
+__global__ void k_static_meta(const __grid_constant__ Dims p, Meta* m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t o = 0, e = 0, w = 0;
+  for (int i = 0; i < p.n; ++i) {
+    const int d = p.d[i];
+    m->dims[i] = d;
+    m->offs[i] = o;
+    m->eoffs[i] = e;
+    m->woffs[i] = d > kShmemDim ? w : 0;
+    o += int64_t(d) * d;
+    e += d;
+    if (d > kShmemDim) w += 2 * int64_t(d) * d;
+  }
+}
 
 }  // namespace
 
@@ -61,21 +88,14 @@ extern "C" int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, co
     B2_REQUIRE(n_mat >= 0 && n_mat <= kMaxMats, B2_EINVAL,
                "b2_eigh_batched_static takes at most 1024 matrices");
     B2_CUDA(cudaSetDevice(ctx->c.device));
-    Meta& m = t_meta;
-    int64_t o = 0, e = 0, w = 0;
+    Dims p;
+    p.n = n_mat;
+    int64_t w = 0;
     int max_dim = 0;
     for (int i = 0; i < n_mat; ++i) {
       B2_REQUIRE(dims[i] >= 1 && dims[i] <= 1024, B2_EINVAL, "dims must be in [1, 1024]");
-      m.dims[i] = dims[i];
-      m.offs[i] = o;
-      m.eoffs[i] = e;
-      m.woffs[i] = 0;
-      o += int64_t(dims[i]) * dims[i];
-      e += dims[i];
-      if (dims[i] > kShmemDim) {
-        m.woffs[i] = w;
-        w += 2 * int64_t(dims[i]) * dims[i];
-      }
+      p.d[i] = uint16_t(dims[i]);
+      if (dims[i] > kShmemDim) w += 2 * int64_t(dims[i]) * dims[i];
       max_dim = dims[i] > max_dim ? dims[i] : max_dim;
     }
     B2_REQUIRE(w <= kWorkDoubles, B2_EINVAL,
@@ -83,12 +103,16 @@ extern "C" int b2_eigh_batched_static(b2_ctx ctx, int n_mat, const int* dims, co
                "their sum exceeds the 524288 available (4 MiB)");
     if (n_mat == 0) return B2_OK;
     double* base = scratch_address(ctx->c.device);
-    B2_CUDA(cudaMemcpyAsync(base, &m, sizeof(Meta), cudaMemcpyHostToDevice, ctx->c.stream));
-    char* meta = reinterpret_cast<char*>(base);
-    const int* d_dims = reinterpret_cast<const int*>(meta + offsetof(Meta, dims));
-    const int64_t* d_offs = reinterpret_cast<const int64_t*>(meta + offsetof(Meta, offs));
-    const int64_t* d_eoffs = reinterpret_cast<const int64_t*>(meta + offsetof(Meta, eoffs));
-    const int64_t* d_woffs = reinterpret_cast<const int64_t*>(meta + offsetof(Meta, woffs));
+    Meta* meta = reinterpret_cast<Meta*>(base);
+    k_static_meta<<<1, 32, 0, ctx->c.stream>>>(p, meta);
+    b2k::count_launches(1);
+    B2_CUDA(cudaGetLastError());
+    // device addresses of the tables (offsets into the array; nothing is dereferenced here)
+    char* mb = reinterpret_cast<char*>(base);
+    const int* d_dims = reinterpret_cast<const int*>(mb + offsetof(Meta, dims));
+    const int64_t* d_offs = reinterpret_cast<const int64_t*>(mb + offsetof(Meta, offs));
+    const int64_t* d_eoffs = reinterpret_cast<const int64_t*>(mb + offsetof(Meta, eoffs));
+    const int64_t* d_woffs = reinterpret_cast<const int64_t*>(mb + offsetof(Meta, woffs));
     b2k::launch_jacobi(n_mat, d_dims, d_offs, d_eoffs, a, evals, evecs, base + kMetaDoubles,
                        d_woffs, max_dim, ctx->c.stream);
     B2_CUDA(cudaGetLastError());

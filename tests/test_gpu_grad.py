@@ -176,3 +176,34 @@ def test_grad_full_size_identities(ctx):
     b2.b2_free_env(env)
     b2.b2_free_mps(s)
     b2.b2_free_mpo(m)
+
+
+def test_grad_n24_M500_against_oracle_transfer_matrices(ctx):
+    # the gradient workload's size (n = 24, N = 24, M = 500, integrals of seed 4): the full
+    # gamma and 160 elements of Gamma / 2 from b2_rdm_grad against the oracle's single-string
+    # transfer-matrix contractions of the same seeded MPS (Sec. 2.5.1 definitions)
+    from oracle import rdm as ordm
+    from synth import config_integrals, occupancies, random_mps, sector_sizes
+    h, eri, N, tsz, kind = config_integrals("abinitio_n24")
+    n, M = 24, 500
+    bonds = sector_sizes(n, N, tsz, M, occupancies(n, N, kind))
+    sites = random_mps(bonds, seed=104, center=0)
+    m = b2.b2_build_mpo(ctx, h, eri, 0.0, N, tsz)
+    s = b2.b2_mps_import(ctx, bonds, sites, N, tsz, center=0)
+    g1, g2 = b2.b2_rdm_grad(ctx, m, s, n)
+    pairs = [(p, q) for p in range(n) for q in range(n)]
+    rng = np.random.default_rng(24)
+    quads = [tuple(int(v) for v in rng.integers(0, n, 4)) for _ in range(140)]
+    # coinciding indices and the ends of the chain
+    quads += [(0, 0, 23, 23), (23, 0, 0, 23), (5, 5, 5, 5), (11, 12, 12, 11), (3, 9, 9, 3),
+              (0, 23, 23, 0), (12, 12, 13, 13), (7, 8, 9, 10), (22, 1, 2, 21), (4, 4, 4, 17),
+              (17, 4, 4, 4), (1, 1, 1, 1), (20, 2, 20, 2), (2, 20, 2, 20), (10, 10, 10, 9),
+              (9, 10, 10, 10), (6, 19, 13, 0), (0, 13, 19, 6), (15, 15, 16, 16), (16, 15, 15, 16)]
+    g_ref, G_ref = ordm.rdm_elements_mps(bonds, sites, pairs, quads)
+    assert np.abs(g1.ravel() - g_ref).max() <= 1e-11
+    G_gpu = np.array([2.0 * g2[q4] for q4 in quads])
+    assert np.abs(G_gpu - G_ref).max() <= 1e-11
+    # the comparison is not vacuous: many of the sampled elements are far from zero
+    assert np.sum(np.abs(G_ref) > 1e-3) > 40
+    b2.b2_free_mps(s)
+    b2.b2_free_mpo(m)

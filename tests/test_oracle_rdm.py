@@ -106,3 +106,50 @@ def test_mps_state_matches_oracle_heff_energy_and_norm():
     assert abs(e_fci - e_heff) < 1e-11
     gamma, Gamma = rdm.mps_rdm12(bonds, sites, n, 0)
     assert abs(_energy(h, eri, 0.0, gamma, Gamma) - e_fci) < 1e-11
+
+
+@pytest.mark.parametrize("n,n_elec,two_sz,M,center,seed", [
+    (5, 5, 1, 12, 0, 31),    # open shell, centre at site 0
+    (6, 6, 0, 20, 0, 32),
+    (6, 4, 0, 16, 2, 33),    # norm carried by an inner site
+])
+def test_transfer_matrix_rdm_matches_the_determinant_route(n, n_elec, two_sz, M, center, seed):
+    # the single-string transfer-matrix contraction (used where the state is far too large
+    # for the determinant basis) against the definition evaluated on the FCI-sized vector;
+    # the MPS is scaled by 3 so that the division by the norm is exercised
+    bonds = sector_sizes(n, n_elec, two_sz, M, occupancies(n, n_elec, "ab_initio"))
+    sites = random_mps(bonds, seed=seed, center=center)
+    sites = [{k: (3.0 * v if i == center else v) for k, v in blk.items()}
+             for i, blk in enumerate(sites)]
+    gamma, Gamma = rdm.mps_rdm12(bonds, sites, n_elec, two_sz)
+    pairs = [(p, q) for p in range(n) for q in range(n)]
+    rng = np.random.default_rng(seed)
+    quads = [tuple(int(x) for x in rng.integers(0, n, 4)) for _ in range(40)]
+    quads += [(0, 0, 1, 1), (1, 2, 2, 1), (n - 1, 0, 0, n - 1), (2, 2, 2, 2)]
+    g, G = rdm.rdm_elements_mps(bonds, sites, pairs, quads)
+    assert np.abs(g - np.array([gamma[p, q] for p, q in pairs])).max() <= 1e-12
+    assert np.abs(G - np.array([Gamma[q4] for q4 in quads])).max() <= 1e-12
+    assert abs(sum(g[p * n + p] for p in range(n)) - n_elec) <= 1e-12
+
+
+def test_jordan_wigner_site_matrices_anticommute():
+    # {a_i, a+_j} = delta_ij and {a_i, a_j} = 0 for the site-by-site representation, checked
+    # on the dense Kronecker products of n = 3 sites (6 modes)
+    n = 3
+
+    def dense(op_list):
+        mats = rdm.jordan_wigner_site_matrices(n, op_list)
+        out = np.ones((1, 1))
+        for m in mats:
+            out = np.kron(out, m)
+        return out
+
+    eye = np.eye(4 ** n)
+    for i in range(2 * n):
+        for j in range(2 * n):
+            ai, adj = dense([(i, False)]), dense([(j, True)])
+            assert np.abs(ai @ adj + adj @ ai - (eye if i == j else 0.0)).max() == 0.0
+            aj = dense([(j, False)])
+            assert np.abs(ai @ aj + aj @ ai).max() == 0.0
+            # a product is the product of the single-operator representations
+            assert np.array_equal(dense([(i, False), (j, True)]), ai @ adj)

@@ -1,7 +1,9 @@
 """b2_eigh_batched_static: the eigensolver entry point for callers that cannot allocate
-device memory (its scratch is a fixed device array in the library).  Its results must
-match the allocating entry point b2_eigh_batched, call after call.  This file is named to
-be collected last, so a run that stops at the first failure has run everything else."""
+device memory -- runtimes that own every byte of device memory through their own pool, or
+loops that must not synchronise with the device for an allocation.  Its scratch is a fixed
+device array in the library.  Its results must match the allocating entry point
+b2_eigh_batched, call after call, and a call must not allocate.  This file is named to be
+collected last, so a run that stops at the first failure has run everything else."""
 import numpy as np
 import pytest
 
@@ -57,6 +59,28 @@ def test_static_eigh_matches_allocating_entry_point():
             assert np.all(np.abs(overlap[iso] - 1.0) < 1e-9)
             eo += d
             vo += d * d
+    ctx.close()
+
+
+def test_static_eigh_allocates_nothing():
+    # the library's context allocates through torch's caching allocator; after a warm-up
+    # call (CUDA's lazy module set-up, the symbol address lookup), further calls of the
+    # static entry point change neither the allocated nor the reserved bytes
+    ctx = b2.Context(0)
+    rng = np.random.default_rng(7)
+    dims = [5, 60, 113, 200]
+    _, flat = _batch(rng, dims)
+    ev = torch.empty(sum(dims), dtype=torch.float64, device=DEV)
+    vec = torch.empty(sum(d * d for d in dims), dtype=torch.float64, device=DEV)
+    b2.b2_eigh_batched_static(ctx, dims, flat, ev, vec)
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(DEV), torch.cuda.memory_reserved(DEV))
+    for _ in range(3):
+        b2.b2_eigh_batched_static(ctx, dims, flat, ev, vec)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(DEV), torch.cuda.memory_reserved(DEV))
+    assert before == after
+    assert np.all(np.isfinite(ev.cpu().numpy()))
     ctx.close()
 
 
