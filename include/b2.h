@@ -61,10 +61,12 @@ enum {
 };
 
 /* Arithmetic of the H_eff contraction.  B2_FP64: FP64 throughout.  B2_BF16X3: each FP64
- * operand split into bf16 hi + lo, products hi*hi + hi*lo + lo*hi on the tensor cores
- * with FP32 accumulation, block results summed in FP64.  B2_BF16X6: three bf16 slices,
- * the six products of order <= 2. */
-typedef enum { B2_FP64 = 0, B2_BF16X3 = 1, B2_BF16X6 = 2 } b2_prec;
+ * operand split into bf16 hi + lo, products hi*hi + hi*lo + lo*hi on the tcgen05 tensor
+ * cores with FP32 accumulation, block results added in FP64 (about 1e-4 relative error per
+ * product).  B2_TF32X3: the same with tf32 hi + lo (22 significant bits, about 1e-6), at
+ * half the tensor-core rate of bf16.  The split products are the mixed-precision path of
+ * the Davidson solver, which refines their result with FP64 products (b2_davidson). */
+typedef enum { B2_FP64 = 0, B2_BF16X3 = 1, B2_TF32X3 = 2 } b2_prec;
 
 typedef struct b2_ctx_s* b2_ctx;
 typedef struct b2_mpo_s* b2_mpo;
@@ -318,14 +320,20 @@ int b2_profile(b2_ctx ctx, int enable);
 int b2_profile_read(b2_ctx ctx, b2_profile_data* out);
 
 /* --------------------------------------------------------------------- test support
- * Shorter device-side limits for tests of the failure paths (no counterpart in the
- * paper): tests make a limit run out on purpose and check the status that comes back,
- * without faulting or hanging anything.  wait_iters: polls of a bounded device wait in the
- * tensor-core contraction before it gives up (0 = the built-in limit, about a second or
- * more) -- a call whose wait ran out returns B2_ETIMEOUT and the context stays usable;
- * jacobi_max_sweeps: sweeps of the truncation eigensolver before b2_sweep reports
- * B2_ENOCONV for a sector still rotating (0 = the built-in 60).  Per context. */
-int b2_debug_limits(b2_ctx ctx, int wait_iters, int jacobi_max_sweeps);
+ * Failure injection for tests of the failure paths (no counterpart in the paper): tests
+ * make a device-side limit run out on purpose and check the status that comes back,
+ * without faulting or hanging anything.  stuck_wait_polls > 0: every CTA of the
+ * tensor-core contraction first waits that many polls on a barrier nothing arrives on, so
+ * the wait runs out, the CTA aborts cleanly (copies and MMAs in flight drained, tensor
+ * memory freed) and the product reports B2_ETIMEOUT (through b2_sync, b2_davidson or
+ * b2_sweep); the context stays usable.  jacobi_max_sweeps > 0: sweeps of the truncation
+ * eigensolver before b2_sweep reports B2_ENOCONV for a sector still rotating (0 = the
+ * built-in 60).  0 / 0 restores normal operation.  Per context. */
+int b2_debug_limits(b2_ctx ctx, int stuck_wait_polls, int jacobi_max_sweeps);
+/* Wait for the context's stream and report what its kernels flagged since the last check:
+ * B2_ETIMEOUT if a bounded device-side wait ran out (the stream-ordered calls return before
+ * their kernels run, so this is where such a failure of b2_heff_apply shows). */
+int b2_sync(b2_ctx ctx);
 
 void b2_free_mpo(b2_mpo mpo);
 void b2_free_mps(b2_mps mps);

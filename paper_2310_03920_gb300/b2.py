@@ -14,8 +14,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libb2.so")
 
 B2_OK, B2_EINVAL, B2_ENOMEM, B2_ECUDA, B2_ENOCONV, B2_ETIMEOUT, B2_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-B2_FP64, B2_BF16X3, B2_BF16X6 = 0, 1, 2
-PRECISIONS = {"fp64": B2_FP64, "bf16x3": B2_BF16X3, "bf16x6": B2_BF16X6}
+B2_FP64, B2_BF16X3, B2_TF32X3 = 0, 1, 2
+PRECISIONS = {"fp64": B2_FP64, "bf16x3": B2_BF16X3, "tf32x3": B2_TF32X3}
 _ERRNAMES = {-1: "B2_EINVAL", -2: "B2_ENOMEM", -3: "B2_ECUDA", -4: "B2_ENOCONV",
              -5: "B2_ETIMEOUT", -6: "B2_EUNSUPPORTED"}
 
@@ -77,6 +77,7 @@ _sig = {
     "b2_davidson_batched": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(DavOpts), _vp, _vp, _vp]),
     "b2_sweep_batched": (_i, [_vp, _i, _vp, ctypes.POINTER(SweepOpts), _vp]),
     "b2_debug_limits": (_i, [_vp, _i, _i]),
+    "b2_sync": (_i, [_vp]),
     "b2_profile": (_i, [_vp, _i]),
     "b2_profile_read": (_i, [_vp, ctypes.POINTER(ProfileData)]),
     "b2_free_mpo": (None, [_vp]),
@@ -348,8 +349,12 @@ def b2_rdm_grad(ctx, mpo, mps, n):
     return g1, g2
 
 
-def b2_debug_limits(ctx, wait_iters=0, jacobi_max_sweeps=0):
-    _check(ctx.h, lib.b2_debug_limits(ctx.h, wait_iters, jacobi_max_sweeps))
+def b2_debug_limits(ctx, stuck_wait_polls=0, jacobi_max_sweeps=0):
+    _check(ctx.h, lib.b2_debug_limits(ctx.h, stuck_wait_polls, jacobi_max_sweeps))
+
+
+def b2_sync(ctx):
+    _check(ctx.h, lib.b2_sync(ctx.h))
 
 
 def b2_profile(ctx, enable=True):

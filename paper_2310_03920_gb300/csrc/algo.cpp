@@ -255,7 +255,8 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
 // the returned vector.
 DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o) {
   if (o.prec == B2_FP64) return davidson_core(env, site, psi, o, B2_FP64, nullptr, o.conv_tol);
-  B2_REQUIRE(o.prec == B2_BF16X3, B2_EUNSUPPORTED, "precision not implemented in this build");
+  B2_REQUIRE(o.prec == B2_BF16X3 || o.prec == B2_TF32X3, B2_EUNSUPPORTED,
+             "precision not implemented in this build");
   Ctx* c = env->ctx;
   WindowProgram& wp = window_program(env, site);
   const int64_t n = wp.psi.size;

@@ -236,8 +236,8 @@ int b2_heff_apply(b2_ctx ctx, b2_env env, int site, const double* psi, double* o
     check_env(ctx, env);
     B2_REQUIRE(psi && out, B2_EINVAL, "null vector");
     B2_REQUIRE(std::isfinite(e_shift), B2_EINVAL, "non-finite shift");
-    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3, B2_EUNSUPPORTED,
-               "precision not implemented in this build (B2_FP64, B2_BF16X3 are)");
+    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3 || prec == B2_TF32X3, B2_EINVAL,
+               "unknown precision (B2_FP64, B2_BF16X3, B2_TF32X3)");
     ensure_device(ctx);
     auto& wp = b2::window_program(env, site);
     B2_REQUIRE(!overlap(psi, out, wp.psi.size), B2_EINVAL, "psi and out overlap");
@@ -319,8 +319,8 @@ int b2_heff_apply_batched(b2_ctx ctx, int n, const b2_env* envs, const int* site
     B2_REQUIRE(n >= 0, B2_EINVAL, "n < 0");
     if (n == 0) return;
     B2_REQUIRE(envs && sites && psis && outs, B2_EINVAL, "null argument");
-    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3, B2_EUNSUPPORTED,
-               "precision not implemented in this build");
+    B2_REQUIRE(prec == B2_FP64 || prec == B2_BF16X3 || prec == B2_TF32X3, B2_EINVAL,
+               "unknown precision (B2_FP64, B2_BF16X3, B2_TF32X3)");
     for (int i = 0; i < n; ++i) check_env(ctx, envs[i]);
     ensure_device(ctx);
     b2::heff_apply_batched(&ctx->c, n, envs, sites, psis, outs, prec, algo_flops);
@@ -374,12 +374,23 @@ int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri
   });
 }
 
-int b2_debug_limits(b2_ctx ctx, int wait_iters, int jacobi_max_sweeps) {
+int b2_debug_limits(b2_ctx ctx, int stuck_wait_polls, int jacobi_max_sweeps) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx, B2_EINVAL, "null context");
-    B2_REQUIRE(wait_iters >= 0 && jacobi_max_sweeps >= 0, B2_EINVAL, "limits must be >= 0");
-    ctx->c.wait_limit = uint32_t(wait_iters);
+    B2_REQUIRE(stuck_wait_polls >= 0 && jacobi_max_sweeps >= 0, B2_EINVAL, "limits must be >= 0");
+    ctx->c.stuck_polls = uint32_t(stuck_wait_polls);
     ctx->c.jacobi_max_sweeps = jacobi_max_sweeps;
+  });
+}
+
+int b2_sync(b2_ctx ctx) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(ctx, B2_EINVAL, "null context");
+    ensure_device(ctx);
+    B2_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    B2_CUDA(cudaGetLastError());
+    B2_REQUIRE(ctx->c.take_status() == 0, B2_ETIMEOUT,
+               "a bounded device-side wait ran out since the last check");
   });
 }
 

@@ -247,7 +247,8 @@ std::vector<DavidsonResult> davidson_batched(Ctx* c, const std::vector<b2_env_s*
     for (int i = 0; i < np; ++i) out[i] = st[i].res;
     return out;
   }
-  B2_REQUIRE(o.prec == B2_BF16X3, B2_EUNSUPPORTED, "precision not implemented in this build");
+  B2_REQUIRE(o.prec == B2_BF16X3 || o.prec == B2_TF32X3, B2_EUNSUPPORTED,
+             "precision not implemented in this build");
   // mixed-precision refinement (davidson in algo.cpp), all problems in lockstep
   const int rounds = o.refine_max > 0 ? o.refine_max : 4;
   const int max_inner = o.max_iter > 0 ? o.max_iter : 30;

@@ -53,9 +53,9 @@ struct Ctx {
   void* user = nullptr;
   std::string last_error;
   int* d_status = nullptr;   // device status words: [0] bounded waits, [1] Jacobi limit (0 = ok)
-  // limits that tests can shorten (b2_debug_limits); 0 = the built-in defaults
+  // failure-path test settings (b2_debug_limits); 0 = off / the built-in defaults
   int jacobi_max_sweeps = 0;
-  uint32_t wait_limit = 0;
+  uint32_t stuck_polls = 0;
   // side streams and fork/join events (created on first use) for concurrent kernels
   static constexpr int kSides = 4;
   cudaStream_t side[kSides] = {};

@@ -66,11 +66,10 @@ double term_tile_flops(const GemmTerm& t) {
 }
 }  // namespace
 
-void GemmProgram::finalize(Ctx* c, bool with_tc) {
+void GemmProgram::finalize(Ctx* c) {
   terms.clear();
   tasks.clear();
   reds.clear();
-  tiles_tc.clear();
   std::vector<double> tcost;   // per term
   double total = 0;
   for (size_t i = 0; i < outs.size(); ++i) {
@@ -121,9 +120,6 @@ void GemmProgram::finalize(Ctx* c, bool with_tc) {
           for (const auto& rg : ranges) tasks.push_back({int(i), r, cc, rg.first, rg.second, slots++});
         }
       }
-    if (with_tc)
-      for (int r = 0; r < o.M; r += b2k::kTcTile)
-        for (int cc = 0; cc < o.N; cc += b2k::kTcTile) tiles_tc.push_back({int(i), r, cc});
   }
   // most expensive items first (they are dispatched first)
   std::vector<double> cost(tasks.size());
@@ -146,21 +142,12 @@ void GemmProgram::finalize(Ctx* c, bool with_tc) {
   upload(c, d_tasks, tasks);
   upload(c, d_reds, reds);
   if (slots > 0) d_partial.reset(c, sizeof(double) * size_t(slots) * b2k::kTile * b2k::kTile);
-  if (with_tc) upload(c, d_tiles_tc, tiles_tc);
 }
 
 void GemmProgram::launch(Ctx* c, const BufTable& bt) const {
   b2k::launch_gemm(d_tasks.as<b2k::GemmTask>(), int(tasks.size()), d_reds.as<b2k::GemmReduce>(),
                    int(reds.size()), d_partial.as<double>(), d_outs.as<b2k::GemmOut>(),
                    d_terms.as<GemmTerm>(), bt, c->stream);
-  B2_CUDA(cudaGetLastError());
-}
-
-void GemmProgram::launch_tc(Ctx* c, const BufTable& bt) const {
-  B2_REQUIRE(d_tiles_tc.ptr != nullptr || tiles_tc.empty(), B2_EINVAL,
-             "internal: program finalized without tensor-core tiles");
-  b2k::launch_gemm_tc(d_tiles_tc.as<b2k::GemmTile>(), int(tiles_tc.size()), d_outs.as<b2k::GemmOut>(),
-                      d_terms.as<GemmTerm>(), bt, c->status(), c->stream);
   B2_CUDA(cudaGetLastError());
 }
 
@@ -635,7 +622,7 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
                  (long long)(combL.size + combR.size), (long long)wp.psi.size);
     for (auto& kv : by_rows) std::fprintf(stderr, "  rows<=%d: %.3f of flops\n", kv.first, kv.second / fl);
   }
-  prog.finalize(c, true);   // FP64 and tensor-core tilings
+  prog.finalize(c);
   int64_t comb_size = combL.size + combR.size;
   if (comb_size > 0) {
     wp.comb_buf.reset(c, size_t(comb_size) * sizeof(double));
@@ -679,36 +666,179 @@ WindowProgram& window_program(b2_env_s* env, int site) {
   return wp;
 }
 
-void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
-                double* flops, b2_prec prec) {
-  WindowProgram& wp = window_program(env, site);
-  Ctx* c = env->ctx;
+// ----------------------------------------------------- split-precision program
+namespace {
+inline int pad16(int x) { return (x + 15) & ~15; }
+inline int elem_bytes(b2_prec p) { return p == B2_TF32X3 ? 4 : 2; }
+
+// Host tables of the tensor-core form of the window's contraction (see TcProgram).
+void build_tc(WindowProgram& wp) {
+  TcProgram& tp = wp.tc;
+  const GemmProgram& g = wp.heff;
+  std::map<std::pair<int, int64_t>, int64_t> env_dst;
+  auto env_operand = [&](int buf, int64_t off, int rows, int cols, int ld) -> int64_t {
+    B2_REQUIRE(ld == cols, B2_EINVAL, "internal: operand block not contiguous");
+    auto key = std::make_pair(buf, off);
+    auto it = env_dst.find(key);
+    if (it != env_dst.end()) return it->second;
+    const int rp = pad16(rows), kp = pad16(cols);
+    const int64_t dst = tp.env_elems;
+    tp.env_elems += int64_t(rp) * kp;
+    tp.env_tasks.push_back({off, dst, rows, cols, ld, 0, rp, kp, buf});
+    env_dst[key] = dst;
+    return dst;
+  };
+  // psi^T blocks: rows m_r, contraction index m_l
+  std::map<int64_t, int64_t> psi_dst;
+  for (const auto& pb : wp.psi.blocks) {
+    const int rp = pad16(pb.mr), kp = pad16(pb.ml);
+    psi_dst[pb.off] = tp.psi_elems;
+    tp.psi_tasks.push_back({pb.off, tp.psi_elems, pb.mr, pb.ml, pb.mr, 1, rp, kp, 0});
+    tp.psi_elems += int64_t(rp) * kp;
+  }
+  std::vector<double> cost;
+  for (size_t i = 0; i < g.outs.size(); ++i) {
+    const b2k::GemmOut& o = g.outs[i];
+    b2k::TcOut to{};
+    to.off = o.off;
+    to.M = o.M;
+    to.N = o.N;
+    to.accumulate = o.accumulate;
+    to.t0 = int(tp.terms.size());
+    double c = 0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const GemmTerm& gt = g.terms[t];
+      B2_REQUIRE(gt.flags == kTransQ && gt.bufX == 0, B2_EINVAL, "internal: H_eff term form");
+      auto ip = psi_dst.find(gt.offX);
+      B2_REQUIRE(ip != psi_dst.end(), B2_EINVAL, "internal: psi block of a term");
+      b2k::TcTerm tt{};
+      tt.offA = env_operand(gt.bufP, gt.offP, o.M, gt.K1, gt.ldP);
+      tt.offB1 = ip->second;
+      tt.offB2 = env_operand(gt.bufQ, gt.offQ, o.N, gt.K2, gt.ldQ);
+      tt.K1 = gt.K1;
+      tt.K2 = gt.K2;
+      tt.alpha = static_cast<float>(gt.alpha);
+      tp.terms.push_back(tt);
+      c += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
+    }
+    to.t1 = int(tp.terms.size());
+    tp.outs.push_back(to);
+    for (int r = 0; r < o.M; r += 128)
+      for (int cc = 0; cc < o.N; cc += 128) {
+        tp.tiles.push_back({int(i), r, cc});
+        cost.push_back(c);
+      }
+  }
+  // most expensive tiles first
+  std::vector<int> order(tp.tiles.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = int(k);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<b2k::TcTile> sorted(tp.tiles.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = tp.tiles[order[k]];
+  tp.tiles.swap(sorted);
+  B2_REQUIRE(tp.terms.size() < (1u << 31), B2_EUNSUPPORTED, "too many contraction terms");
+  tp.built = true;
+}
+
+BufTable window_buffers(b2_env_s* env, int site, WindowProgram& wp, const double* psi, double* out) {
   BufTable bt{};
   bt.p[0] = const_cast<double*>(psi);
   bt.p[1] = out;
   bt.p[2] = env->L[site].data.as<double>();
   bt.p[3] = env->R[site + 2].data.as<double>();
   bt.p[4] = wp.comb_buf.as<double>();
+  return bt;
+}
+
+// precombined operators of the window, once
+void ensure_comb(Ctx* c, WindowProgram& wp, const BufTable& bt) {
   if (!wp.comb_done) {
     if (wp.comb_buf.ptr) wp.comb.launch(c, bt);
     wp.comb_done = true;
   }
+}
+
+// split psi (once per product) into the psi planes of the window's tensor-core program
+void split_psi(Ctx* c, TcProgram& tp, const double* psi, b2_prec prec) {
+  const size_t plane = size_t(std::max<int64_t>(tp.psi_elems, 1)) * elem_bytes(prec);
+  if (tp.psi_planes.bytes < 2 * plane) tp.psi_planes.reset(c, 2 * plane);
+  BufTable bt{};
+  bt.p[0] = const_cast<double*>(psi);
+  uint8_t* hi = tp.psi_planes.as<uint8_t>();
+  b2k::launch_split(tp.d_psi_tasks.as<b2k::SplitTask>(), int(tp.psi_tasks.size()), bt, hi,
+                    hi + plane, prec == B2_TF32X3, c->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+b2k::TcGroup tc_group(TcProgram& tp, b2_prec prec, double* out) {
+  const size_t eplane = size_t(std::max<int64_t>(tp.env_elems, 1)) * elem_bytes(prec);
+  const size_t pplane = size_t(std::max<int64_t>(tp.psi_elems, 1)) * elem_bytes(prec);
+  b2k::TcGroup g{};
+  g.tiles = tp.d_tiles.as<b2k::TcTile>();
+  g.outs = tp.d_outs.as<b2k::TcOut>();
+  g.terms = tp.d_terms.as<b2k::TcTerm>();
+  g.env_hi = tp.env_planes.as<uint8_t>();
+  g.env_lo = g.env_hi + eplane;
+  g.psi_hi = tp.psi_planes.as<uint8_t>();
+  g.psi_lo = g.psi_hi + pplane;
+  g.out = out;
+  g.tile0 = 0;
+  return g;
+}
+}  // namespace
+
+TcProgram& tc_program(b2_env_s* env, int site, b2_prec prec) {
+  B2_REQUIRE(prec == B2_BF16X3 || prec == B2_TF32X3, B2_EUNSUPPORTED, "precision not implemented");
+  WindowProgram& wp = window_program(env, site);
+  Ctx* c = env->ctx;
+  TcProgram& tp = wp.tc;
+  if (!tp.built) {
+    build_tc(wp);
+    upload(c, tp.d_outs, tp.outs);
+    upload(c, tp.d_terms, tp.terms);
+    upload(c, tp.d_tiles, tp.tiles);
+    upload(c, tp.d_env_tasks, tp.env_tasks);
+    upload(c, tp.d_psi_tasks, tp.psi_tasks);
+  }
+  if (tp.env_prec != int(prec)) {
+    BufTable bt = window_buffers(env, site, wp, nullptr, nullptr);
+    ensure_comb(c, wp, bt);
+    const size_t plane = size_t(std::max<int64_t>(tp.env_elems, 1)) * elem_bytes(prec);
+    tp.env_planes.reset(c, 2 * plane);
+    uint8_t* hi = tp.env_planes.as<uint8_t>();
+    b2k::launch_split(tp.d_env_tasks.as<b2k::SplitTask>(), int(tp.env_tasks.size()), bt, hi,
+                      hi + plane, prec == B2_TF32X3, c->stream);
+    B2_CUDA(cudaGetLastError());
+    tp.env_prec = int(prec);
+  }
+  return tp;
+}
+
+void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double e_shift,
+                double* flops, b2_prec prec) {
+  WindowProgram& wp = window_program(env, site);
+  Ctx* c = env->ctx;
+  BufTable bt = window_buffers(env, site, wp, psi, out);
+  ensure_comb(c, wp, bt);
+  TcProgram* tp = prec == B2_FP64 ? nullptr : &tc_program(env, site, prec);
+  if (tp) split_psi(c, *tp, psi, prec);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->prof) {
-    cudaEvent_t e0, e1;
     B2_CUDA(cudaEventCreate(&e0));
     B2_CUDA(cudaEventCreate(&e1));
     B2_CUDA(cudaEventRecord(e0, c->stream));
-    if (prec == B2_FP64)
-      wp.heff.launch(c, bt);
-    else
-      wp.heff.launch_tc(c, bt);
+  }
+  if (!tp) {
+    wp.heff.launch(c, bt);
+  } else {
+    b2k::launch_heff_tc(tc_group(*tp, prec, out), nullptr, 1, int(tp->tiles.size()),
+                        prec == B2_TF32X3, c->status(), c->stuck_polls, c->stream);
+    B2_CUDA(cudaGetLastError());
+  }
+  if (e0) {
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->prof_events.push_back({e0, e1});
     c->prof_flops += wp.heff.flops;
-  } else if (prec == B2_FP64) {
-    wp.heff.launch(c, bt);
-  } else {
-    wp.heff.launch_tc(c, bt);
   }
   if (e_shift != 0.0) b2k::launch_axpby(out, psi, wp.psi.size, 1.0, -e_shift, c->stream);
   if (flops) *flops = wp.heff.flops;
@@ -718,7 +848,7 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
                         const double* const* psis, double* const* outs, b2_prec prec,
                         double* flops) {
   std::vector<b2k::GemmGroup> groups;
-  std::vector<b2k::GemmGroupTc> groups_tc;
+  std::vector<b2k::TcGroup> groups_tc;
   int items = 0, reds = 0, tiles = 0;
   double fl = 0;
   for (int i = 0; i < n; ++i) {
@@ -729,16 +859,8 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
     const int site = sites[i];
     WindowProgram& wp = window_program(env, site);
     B2_REQUIRE(psis[i] != outs[i], B2_EINVAL, "batched H_eff: out aliases psi");
-    BufTable bt{};
-    bt.p[0] = const_cast<double*>(psis[i]);
-    bt.p[1] = outs[i];
-    bt.p[2] = env->L[site].data.as<double>();
-    bt.p[3] = env->R[site + 2].data.as<double>();
-    bt.p[4] = wp.comb_buf.as<double>();
-    if (!wp.comb_done) {
-      if (wp.comb_buf.ptr) wp.comb.launch(c, bt);
-      wp.comb_done = true;
-    }
+    BufTable bt = window_buffers(env, site, wp, psis[i], outs[i]);
+    ensure_comb(c, wp, bt);
     if (prec == B2_FP64) {
       groups.push_back({wp.heff.d_tasks.as<b2k::GemmTask>(), wp.heff.d_reds.as<b2k::GemmReduce>(),
                         wp.heff.d_outs.as<b2k::GemmOut>(), wp.heff.d_terms.as<GemmTerm>(),
@@ -746,9 +868,12 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
       items += int(wp.heff.tasks.size());
       reds += int(wp.heff.reds.size());
     } else {
-      groups_tc.push_back({wp.heff.d_tiles_tc.as<b2k::GemmTile>(), wp.heff.d_outs.as<b2k::GemmOut>(),
-                           wp.heff.d_terms.as<GemmTerm>(), bt, tiles});
-      tiles += int(wp.heff.tiles_tc.size());
+      TcProgram& tp = tc_program(env, site, prec);
+      split_psi(c, tp, psis[i], prec);
+      b2k::TcGroup g = tc_group(tp, prec, outs[i]);
+      g.tile0 = tiles;
+      groups_tc.push_back(g);
+      tiles += int(tp.tiles.size());
     }
     fl += wp.heff.flops;
   }
@@ -766,8 +891,8 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
   } else {
     upload(c, d_groups, groups_tc);
     if (e0) B2_CUDA(cudaEventRecord(e0, c->stream));
-    b2k::launch_gemm_tc_grouped(d_groups.as<b2k::GemmGroupTc>(), int(groups_tc.size()), tiles,
-                                c->status(), c->stream);
+    b2k::launch_heff_tc(b2k::TcGroup{}, d_groups.as<b2k::TcGroup>(), int(groups_tc.size()), tiles,
+                        prec == B2_TF32X3, c->status(), c->stuck_polls, c->stream);
   }
   B2_CUDA(cudaGetLastError());
   if (e0) {

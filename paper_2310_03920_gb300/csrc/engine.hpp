@@ -15,14 +15,12 @@ struct GemmProgram {
   std::vector<b2k::GemmTerm> terms;
   std::vector<b2k::GemmTask> tasks;              // FP64 work items (32x32 tiles, term ranges)
   std::vector<b2k::GemmReduce> reds;             // fixed-order sums of split tiles
-  std::vector<b2k::GemmTile> tiles_tc;           // 128x128 tensor-core tiles
-  DevBuf d_terms, d_outs, d_tasks, d_reds, d_partial, d_tiles_tc;
+  DevBuf d_terms, d_outs, d_tasks, d_reds, d_partial;
   double flops = 0;
   int add_out(uint8_t buf, int64_t off, int M, int N, int ld, bool accumulate);
   void add_term(int out, const b2k::GemmTerm& t);
-  void finalize(Ctx* c, bool with_tc = false);
+  void finalize(Ctx* c);
   void launch(Ctx* c, const b2k::BufTable& bt) const;
-  void launch_tc(Ctx* c, const b2k::BufTable& bt) const;
   bool empty() const { return tasks.empty(); }
 };
 
@@ -66,6 +64,22 @@ struct PsiLayout {
   int find(int jl, int s1, int s2) const { return lookup[(size_t(jl) * 4 + s1) * 4 + s2]; }
 };
 
+// The H_eff contraction in the form of the split-precision tensor-core kernel (tc_heff.cu):
+// outputs, terms and 128 x 128 tiles (most expensive first), the split tasks of the
+// operand blocks the terms use (environments and precombined operators once per window,
+// psi^T once per product) and the split planes ([hi | lo], elements * element size each).
+struct TcProgram {
+  bool built = false;
+  std::vector<b2k::TcOut> outs;
+  std::vector<b2k::TcTerm> terms;
+  std::vector<b2k::TcTile> tiles;
+  std::vector<b2k::SplitTask> env_tasks, psi_tasks;
+  int64_t env_elems = 0, psi_elems = 0;
+  DevBuf d_outs, d_terms, d_tiles, d_env_tasks, d_psi_tasks;
+  DevBuf env_planes, psi_planes;
+  int env_prec = -1;   // precision of the split the env planes hold (-1: none)
+};
+
 struct WindowProgram {
   int site = -1;
   int ver_l = -1, ver_r = -1;
@@ -77,6 +91,7 @@ struct WindowProgram {
   std::vector<b2k::DiagTerm> diag_terms;
   DevBuf d_diag_outs, d_diag_terms;
   bool comb_done = false;
+  TcProgram tc;
 };
 
 }  // namespace b2
@@ -100,6 +115,9 @@ void heff_diag(b2_env_s* env, int site, double* diag);
 // H_eff products of the windows (envs[i], sites[i]) of independent problems on context c
 // in one grouped launch (FP64: k_gemm_grouped + k_gemm_reduce_grouped; split precision:
 // k_gemm_tc_grouped).  Each work item runs exactly the code of the single-problem launch.
+// Split-precision form of window (env, site) for precision prec (host tables, device
+// tables, environment split), built on first use and kept with the window program.
+TcProgram& tc_program(b2_env_s* env, int site, b2_prec prec);
 void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
                         const double* const* psis, double* const* outs, b2_prec prec,
                         double* flops);

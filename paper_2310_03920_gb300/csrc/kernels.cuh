@@ -37,9 +37,6 @@ struct GemmOut {
   int t0, t1;
   uint8_t buf, accumulate;   // accumulate = 0: out is overwritten
 };
-struct GemmTile {
-  int out, r0, c0;
-};
 constexpr int kTile = 32;
 // Work item of the FP64 kernel: the 32 x 32 tile (r0, c0) of output out, summed over the
 // terms [t0, t1) of that output.  slot < 0: the item owns the tile and writes the output;
@@ -109,21 +106,53 @@ struct GemmGroup {
 };
 void launch_gemm_grouped(const GemmGroup* groups, int n_groups, int n_items, int n_reds,
                          cudaStream_t s);
-struct GemmGroupTc {
-  const GemmTile* tiles;
-  const GemmOut* outs;
-  const GemmTerm* terms;
-  BufTable bt;
+// ------------------------------------------------ split-precision tensor-core contraction
+// An operand block split into hi / lo planes in the pre-tiled layout of tc_heff.cu: rows
+// padded to rp = round16(rows), columns (the contraction index) to kp = round16(cols).
+// Element (r, k) of the block is src[r * ld + k], or src[k * ld + r] with trans.  dst: the
+// block's offset in elements of the planes (a multiple of 256).
+struct SplitTask {
+  int64_t src, dst;
+  int rows, cols, ld, trans;
+  int rp, kp;
+  int buf;
+};
+void launch_split(const SplitTask* tasks, int n_tasks, const BufTable& bt, uint8_t* hi,
+                  uint8_t* lo, bool tf32, cudaStream_t s);
+// H_eff output block [M x N] (row-major, ld = N) at element offset off of the output
+// vector, its terms [t0, t1); every term's L operand has M rows and R operand N rows.
+struct TcOut {
+  int64_t off;
+  int M, N;
+  int t0, t1;
+  int accumulate;
+};
+// out += alpha * L [M x K1] psi [K1 x K2] R^T [K2 x N]; offA / offB2: element offsets of the
+// split L and R operands (rows M / N, K = K1 / K2) in the environment planes, offB1: of the
+// split psi^T block (rows K2, K = K1) in the psi planes.
+struct TcTerm {
+  int64_t offA, offB1, offB2;
+  int K1, K2;
+  float alpha;
+};
+struct TcTile {
+  int out, r0, c0;
+};
+// One problem of a launch: tiles, outputs and terms, the split planes and the FP64 output;
+// tile0 is the grid index of its first tile (groups in increasing order).
+struct TcGroup {
+  const TcTile* tiles;
+  const TcOut* outs;
+  const TcTerm* terms;
+  const uint8_t *env_hi, *env_lo, *psi_hi, *psi_lo;
+  double* out;
   int tile0;
 };
-void launch_gemm_tc_grouped(const GemmGroupTc* groups, int n_groups, int n_tiles, int* status,
-                            cudaStream_t s);
-// Split-precision (bf16 hi/lo, three products, FP32 accumulation in TMEM) version of
-// launch_gemm on the tcgen05 tensor cores; tiles are kTcTile x kTcTile.  A bounded wait that
-// runs out writes 1 to *status.
-constexpr int kTcTile = 128;
-void launch_gemm_tc(const GemmTile* tiles, int n_tiles, const GemmOut* outs, const GemmTerm* terms,
-                    const BufTable& bt, int* status, cudaStream_t s);
+// One CTA per 128 x 128 output tile, over all groups' tiles (groups: device table of
+// n_groups problems, or nullptr for the single problem g0); tf32: tf32 x3, else bf16 x3.
+// A bounded wait that runs out writes 1 to *status; stuck_polls > 0 (tests) injects one.
+void launch_heff_tc(const TcGroup& g0, const TcGroup* groups, int n_groups, int n_tiles, bool tf32,
+                    int* status, uint32_t stuck_polls, cudaStream_t s);
 void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
                  const BufTable& bt, cudaStream_t s);
 void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,

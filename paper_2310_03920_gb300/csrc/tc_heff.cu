@@ -1,0 +1,613 @@
+// Split-precision H_eff contraction on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Operands.  Every FP64 operand a is split once into hi + lo (bf16 x3: hi = bf16(a),
+// lo = bf16(a - hi); tf32 x3: the same with tf32, i.e. FP32 with 13 low mantissa bits
+// dropped) and stored "pre-tiled": a block of R rows (the M or N index of the product) and
+// K columns (the contraction index) is padded with zeros to Rp = round16(R) rows and
+// Kp = round16(K) columns and laid out in 128-byte chunks of K; chunk c holds, for every
+// 8-row group, the 16-byte pieces of its kg_c k-groups ([row group][k-group][row][16 B]).
+// This is the canonical K-major no-swizzle operand layout of tcgen05 (8 x 16-byte core
+// matrices, LBO = 128 bytes between k-groups, SBO = kg_c * 128 bytes between row groups),
+// so a 128-row sub-tile of one K chunk is one contiguous run of bytes that a single
+// cp.async.bulk moves into shared memory.  The environments (and their precombined
+// operators) are split once per window and reused by every Davidson product; psi is split
+// (transposed: rows = its columns m_r, K = its rows m_l) once per product.
+//
+// Contraction.  An output tile (128 rows x <= 128 columns of one psi block) receives
+//   sum over terms t, over 128-byte chunks c of K2 = m_r:
+//     T   = L_t[tile rows, :] psi_t[:, c]          (MMA1, FP32 in TMEM, K = m_l)
+//     T'  = split(alpha_t * T)                     (TMEM -> registers -> shared memory)
+//     acc += T' R_t[tile cols, c]^T                 (MMA2, FP32 in TMEM)
+// each product formed as hi*hi + hi*lo + lo*hi; acc is added to the FP64 output block at
+// the end (overwritten or accumulated).
+//
+// Roles (6 warps): warp 0 streams operand chunks through a 3-stage shared-memory ring with
+// cp.async.bulk (completion on the stage's mbarrier); one thread of warp 1 issues the MMAs;
+// warps 2-5 (one per TMEM lane quarter) convert T into T' and write the result.  The MMA
+// thread computes T of the next chain unit while the converter works on the current one
+// (two T buffers in TMEM, two T' buffers in shared memory).  Every wait is bounded: a wait
+// that runs out sets the CTA's abort flag and the status word; the other roles then stop,
+// the producer waits (with the full limit) for its copies in flight, the MMA thread for its
+// MMAs, TMEM is freed and the CTA returns.  For tests of that path, stuck_polls > 0 makes
+// the MMA thread first wait that many polls on a barrier nothing arrives on.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace b2k {
+
+namespace {
+
+constexpr int kStages = 3;
+constexpr int kPBytes = 128 * 128;                   // <= 128 rows x one 128-byte K chunk
+constexpr int kQBytes = 64 * 128;                    // <= 64 rows (one T chunk of psi^T)
+constexpr int kStageBytes = 2 * kPBytes + 2 * kQBytes;
+constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo
+constexpr int kDynSmem = kStages * kStageBytes + 2 * kTpBytes + 1024;
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 256;                       // T0 [0,64), T1 [64,128), acc [128,256)
+constexpr uint32_t kDefaultWait = 1u << 22;
+constexpr uint32_t kDrainWait = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major no-swizzle shared-memory descriptor: start, LBO = 128 (k-groups), SBO (row groups)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+  uint64_t d = uint64_t((addr >> 4) & 0x3FFF);
+  d |= uint64_t(128 >> 4) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+  d |= uint64_t(1) << 46;   // descriptor version of tcgen05
+  return d;
+}
+
+// instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = n;
+// operand type 1 = bf16 (kind::f16), 2 = tf32 (kind::tf32)
+__device__ __forceinline__ uint32_t idesc(int n, bool tf32) {
+  const uint32_t ty = tf32 ? 2u : 1u;
+  return (1u << 4) | (ty << 7) | (ty << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(bool tf32, uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t accum) {
+  if (tf32)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait that also gives up once another role has aborted the CTA
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                         volatile int* abort_flag) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (bar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  return false;
+}
+
+// bounded wait used while draining: never cut short
+__device__ __forceinline__ bool bar_drain(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kDrainWait; ++it)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// tf32 rounding of an FP32 value: nearest on the magnitude (ties away from zero), the 13
+// low mantissa bits cleared
+__device__ __forceinline__ uint32_t tf32_bits(float f) {
+  return (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u;
+}
+
+// split f into (hi, lo) of the operand type, packed as raw bits: bf16 -> 16 bits each
+__device__ __forceinline__ void split_bf16(float f, uint16_t& hi, uint16_t& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(f);
+  const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
+}
+__device__ __forceinline__ void split_tf32(float f, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(f);
+  lo = tf32_bits(f - __uint_as_float(hi));
+}
+
+__host__ __device__ __forceinline__ int pad16(int x) { return (x + 15) & ~15; }
+
+// chain units of one tile: (term t, 128-byte chunk c of K2), terms in order
+struct Unit {
+  int t, c;
+};
+
+}  // namespace
+
+// byte offset of chunk c of a pre-tiled block of rp rows (chunks before c are full)
+__host__ __device__ __forceinline__ int64_t tc_chunk_off(int rp, int c) {
+  return int64_t(c) * rp * 128;
+}
+// k-groups (16 bytes) of chunk c of a block with kp padded columns of es-byte elements
+__host__ __device__ __forceinline__ int tc_chunk_kg(int kp, int es, int c) {
+  const int rem = kp * es / 16 - 8 * c;
+  return rem < 8 ? rem : 8;
+}
+
+// ------------------------------------------------------------------ operand split
+// One CTA per block: every 16-byte piece (row r, k-group j) of the padded pre-tiled block,
+// rows fastest so that consecutive threads read consecutive rows.
+__global__ void __launch_bounds__(256) k_split(const SplitTask* __restrict__ tasks,
+                                               BufTable bt, uint8_t* hi, uint8_t* lo, int tf32) {
+  const SplitTask tk = tasks[blockIdx.x];
+  const double* src = bt.p[tk.buf] + tk.src;
+  const int es = tf32 ? 4 : 2;
+  const int per = 16 / es;                     // elements per 16-byte piece
+  const int kgt = tk.kp * es / 16;             // k-groups over all chunks
+  const int64_t n_units = int64_t(tk.rp) * kgt;
+  const int64_t base = tk.dst * es;
+  for (int64_t u = threadIdx.x; u < n_units; u += blockDim.x) {
+    const int r = int(u % tk.rp), j = int(u / tk.rp);
+    const int c = j >> 3, jj = j & 7;
+    const int kg = tc_chunk_kg(tk.kp, es, c);
+    const int64_t off = base + tc_chunk_off(tk.rp, c) + int64_t(r >> 3) * kg * 128 + jj * 128 + (r & 7) * 16;
+    float f[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = j * per + e;
+      double v = 0.0;
+      if (e < per && r < tk.rows && k < tk.cols)
+        v = tk.trans ? src[int64_t(k) * tk.ld + r] : src[int64_t(r) * tk.ld + k];
+      f[e] = static_cast<float>(v);
+    }
+    uint4 h, l;
+    if (tf32) {
+      uint32_t hh[4], ll[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_tf32(f[e], hh[e], ll[e]);
+      h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+      l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+    } else {
+      uint16_t hh[8], ll[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) split_bf16(f[e], hh[e], ll[e]);
+      h = make_uint4(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16),
+                     hh[4] | (uint32_t(hh[5]) << 16), hh[6] | (uint32_t(hh[7]) << 16));
+      l = make_uint4(ll[0] | (uint32_t(ll[1]) << 16), ll[2] | (uint32_t(ll[3]) << 16),
+                     ll[4] | (uint32_t(ll[5]) << 16), ll[6] | (uint32_t(ll[7]) << 16));
+    }
+    *reinterpret_cast<uint4*>(hi + off) = h;
+    *reinterpret_cast<uint4*>(lo + off) = l;
+  }
+}
+
+// ------------------------------------------------------------------ the contraction
+__device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile, int* status,
+                                             uint32_t stuck_polls, bool tf32) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ __align__(8) uint64_t tfull[2], tempty[2], tpready[2], tpempty[2], accb, drainb;
+  __shared__ __align__(8) uint64_t neverb;   // nothing arrives on it (failure-path tests)
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stage_mem = base;
+  unsigned char* tp_mem = base + kStages * kStageBytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int es = tf32 ? 4 : 2;
+  const int wk = 128 / es;   // elements in one 128-byte K chunk (= T columns per unit)
+  const TcOut o = G.outs[tile.out];
+  const int r0 = tile.r0, c0 = tile.c0;
+  const int n2 = pad16(min(128, o.N - c0));           // MMA2 N (acc columns)
+  const int rowsA = min(128, pad16(o.M) - r0);        // L rows loaded for this tile
+  const int rowsB2 = min(128, pad16(o.N) - c0);       // R rows loaded for this tile
+  const uint32_t limit = kDefaultWait;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&tfull[b], 1);
+      bar_init(&tempty[b], 128);
+      bar_init(&tpready[b], 128);
+      bar_init(&tpempty[b], 1);
+    }
+    bar_init(&accb, 1);
+    bar_init(&drainb, 1);
+    bar_init(&neverb, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicExch(status, 1);
+  };
+  auto nchunks = [&](int k) { return (pad16(k) * es + 127) / 128; };
+  auto next = [&](Unit& u) {
+    if (++u.c >= nchunks(G.terms[u.t].K2)) {
+      ++u.t;
+      u.c = 0;
+    }
+  };
+  const Unit first{o.t0, 0};
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t item = 0;
+      bool ok = true;
+      auto acquire = [&](int& s) -> bool {
+        s = int(item % kStages);
+        if (item >= kStages && !bar_wait(&empty[s], ((item / kStages) & 1) ^ 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          return false;
+        }
+        return true;
+      };
+      auto produce_x = [&](const Unit& u) -> bool {
+        const TcTerm tm = G.terms[u.t];
+        const int kp1 = pad16(tm.K1), rp1 = pad16(tm.K2);
+        const int rowsB1 = min(wk, rp1 - u.c * wk);
+        for (int c = 0; c < nchunks(tm.K1); ++c) {
+          int s;
+          if (!acquire(s)) return false;
+          const int kg = tc_chunk_kg(kp1, es, c);
+          const uint32_t bA = uint32_t(rowsA) * kg * 16, bB = uint32_t(rowsB1) * kg * 16;
+          const int64_t oA = tm.offA * es + tc_chunk_off(pad16(o.M), c) + int64_t(r0 >> 3) * kg * 128;
+          const int64_t oB = tm.offB1 * es + tc_chunk_off(rp1, c) + int64_t((u.c * wk) >> 3) * kg * 128;
+          unsigned char* st = stage_mem + s * kStageBytes;
+          bar_expect_tx(&full[s], 2 * (bA + bB));
+          bulk_g2s(smem_u32(st), G.env_hi + oA, bA, &full[s]);
+          bulk_g2s(smem_u32(st + kPBytes), G.env_lo + oA, bA, &full[s]);
+          bulk_g2s(smem_u32(st + 2 * kPBytes), G.psi_hi + oB, bB, &full[s]);
+          bulk_g2s(smem_u32(st + 2 * kPBytes + kQBytes), G.psi_lo + oB, bB, &full[s]);
+          ++item;
+        }
+        return true;
+      };
+      auto produce_y = [&](const Unit& u) -> bool {
+        const TcTerm tm = G.terms[u.t];
+        const int kp2 = pad16(tm.K2);
+        int s;
+        if (!acquire(s)) return false;
+        const int kg = tc_chunk_kg(kp2, es, u.c);
+        const uint32_t b = uint32_t(rowsB2) * kg * 16;
+        const int64_t oR = tm.offB2 * es + tc_chunk_off(pad16(o.N), u.c) + int64_t(c0 >> 3) * kg * 128;
+        unsigned char* st = stage_mem + s * kStageBytes;
+        bar_expect_tx(&full[s], 2 * b);
+        bulk_g2s(smem_u32(st), G.env_hi + oR, b, &full[s]);
+        bulk_g2s(smem_u32(st + kPBytes), G.env_lo + oR, b, &full[s]);
+        ++item;
+        return true;
+      };
+      Unit ux = first, uy = first;
+      if (ux.t < o.t1) {
+        ok = produce_x(ux);
+        next(ux);
+      }
+      while (ok && uy.t < o.t1 && !abort_flag) {
+        if (ux.t < o.t1) {
+          ok = produce_x(ux);
+          next(ux);
+          if (!ok) break;
+        }
+        ok = produce_y(uy);
+        next(uy);
+      }
+      // drain: the copies of the last item of every stage have landed
+      for (int s = 0; s < kStages; ++s) {
+        if (uint32_t(s) >= item) continue;
+        const uint32_t last = item - 1 - ((item - 1 - s) % kStages);
+        if (!bar_drain(&full[s], (last / kStages) & 1)) fail();
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t item = 0;
+      bool ok = true, started = false;
+      const uint32_t t_base = tmem, acc_tm = tmem + 128;
+      const uint32_t id2 = idesc(n2, tf32);
+      auto take = [&](int& s) -> bool {
+        s = int(item % kStages);
+        if (!bar_wait(&full[s], (item / kStages) & 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          return false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return true;
+      };
+      auto mma1 = [&](const Unit& u, uint32_t idx) -> bool {
+        const int b = idx & 1;
+        if (idx >= 2 && !bar_wait(&tempty[b], ((idx >> 1) & 1) ^ 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          return false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const TcTerm tm = G.terms[u.t];
+        const int kp1 = pad16(tm.K1);
+        const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
+        const uint32_t id1 = idesc(n1, tf32);
+        const uint32_t tT = t_base + uint32_t(b * 64);
+        for (int c = 0; c < nchunks(tm.K1); ++c) {
+          int s;
+          if (!take(s)) return false;
+          const int kg = tc_chunk_kg(kp1, es, c);
+          const uint32_t sbo = uint32_t(kg) * 128;
+          const uint32_t st = smem_u32(stage_mem + s * kStageBytes);
+          const uint32_t aH = st, aL = st + kPBytes, bH = st + 2 * kPBytes, bL = st + 2 * kPBytes + kQBytes;
+          for (int ks = 0; ks < kg / 2; ++ks) {
+            const uint32_t off = uint32_t(ks) * 256;
+            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bH + off, sbo), id1, (c > 0 || ks > 0) ? 1u : 0u);
+            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bL + off, sbo), id1, 1u);
+            mma(tf32, tT, sdesc(aL + off, sbo), sdesc(bH + off, sbo), id1, 1u);
+          }
+          commit(&empty[s]);
+          ++item;
+        }
+        commit(&tfull[b]);
+        return true;
+      };
+      auto mma2 = [&](const Unit& u, uint32_t idx) -> bool {
+        const int b = idx & 1;
+        if (!bar_wait(&tpready[b], (idx >> 1) & 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          return false;
+        }
+        int s;
+        if (!take(s)) return false;
+        const TcTerm tm = G.terms[u.t];
+        const int kg = tc_chunk_kg(pad16(tm.K2), es, u.c);
+        const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
+        const int ksteps = n1 * es / 32;
+        const uint32_t st = smem_u32(stage_mem + s * kStageBytes);
+        const uint32_t tpH = smem_u32(tp_mem + b * kTpBytes), tpL = tpH + kPBytes;
+        const uint32_t sbo = uint32_t(kg) * 128;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t off = uint32_t(ks) * 256;
+          mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + off, sbo), id2,
+              (started || ks > 0) ? 1u : 0u);
+          mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + kPBytes + off, sbo), id2, 1u);
+          mma(tf32, acc_tm, sdesc(tpL + off, 1024), sdesc(st + off, sbo), id2, 1u);
+        }
+        started = true;
+        commit(&empty[s]);
+        commit(&tpempty[b]);
+        ++item;
+        return true;
+      };
+      Unit ux = first, uy = first;
+      uint32_t ix = 0, iy = 0;
+      if (stuck_polls) {
+        // failure-path test: a bounded wait on a barrier nothing arrives on runs out
+        if (!bar_wait(&neverb, 0, stuck_polls, &abort_flag) && !abort_flag) fail();
+        ok = false;
+      }
+      if (ok && ux.t < o.t1) {
+        ok = mma1(ux, ix++);
+        next(ux);
+      }
+      while (ok && uy.t < o.t1) {
+        if (ux.t < o.t1) {
+          ok = mma1(ux, ix++);
+          next(ux);
+          if (!ok) break;
+        }
+        ok = mma2(uy, iy++);
+        next(uy);
+      }
+      // accumulator complete (also with no MMA at all); then every MMA issued has finished
+      commit(&accb);
+      commit(&drainb);
+      if (!bar_drain(&drainb, 0)) fail();
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ converter and epilogue
+    const int quad = warp & 3;              // TMEM lane quarter of this warp
+    const int row = quad * 32 + lane;       // tile row = TMEM lane
+    const uint32_t lane_off = uint32_t(quad * 32) << 16;
+    Unit u = first;
+    uint32_t idx = 0;
+    bool ok = true;
+    // every decision is made uniform over the warp (__all_sync) so that the warp-collective
+    // TMEM loads never run in part of a warp
+    while (u.t < o.t1) {
+      const int b = idx & 1;
+      bool w = bar_wait(&tfull[b], (idx >> 1) & 1, limit, &abort_flag);
+      if (w && idx >= 2) w = bar_wait(&tpempty[b], ((idx >> 1) & 1) ^ 1, limit, &abort_flag);
+      if (!__all_sync(0xffffffffu, w)) {
+        if (!abort_flag) fail();
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const TcTerm tm = G.terms[u.t];
+      const float alpha = tm.alpha;
+      const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
+      unsigned char* tpH = tp_mem + b * kTpBytes;
+      unsigned char* tpL = tpH + kPBytes;
+      const uint32_t rbase = uint32_t(row >> 3) * 1024 + uint32_t(row & 7) * 16;
+      for (int cc = 0; cc < n1; cc += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_off + uint32_t(b * 64 + cc), v);
+        if (tf32) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {   // 4 k-groups of 4 elements
+            uint32_t hh[4], ll[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split_tf32(alpha * v[4 * q + e], hh[e], ll[e]);
+            const uint32_t off = rbase + uint32_t((cc >> 2) + q) * 128;
+            *reinterpret_cast<uint4*>(tpH + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4*>(tpL + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {   // 2 k-groups of 8 elements
+            uint16_t hh[8], ll[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) split_bf16(alpha * v[8 * q + e], hh[e], ll[e]);
+            const uint32_t off = rbase + uint32_t((cc >> 3) + q) * 128;
+            *reinterpret_cast<uint4*>(tpH + off) =
+                make_uint4(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16),
+                           hh[4] | (uint32_t(hh[5]) << 16), hh[6] | (uint32_t(hh[7]) << 16));
+            *reinterpret_cast<uint4*>(tpL + off) =
+                make_uint4(ll[0] | (uint32_t(ll[1]) << 16), ll[2] | (uint32_t(ll[3]) << 16),
+                           ll[4] | (uint32_t(ll[5]) << 16), ll[6] | (uint32_t(ll[7]) << 16));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(&tempty[b]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_arrive(&tpready[b]);
+      next(u);
+      ++idx;
+    }
+    const bool acc_ready = ok && __all_sync(0xffffffffu, bar_wait(&accb, 0, limit, &abort_flag));
+    if (acc_ready) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool any = o.t1 > o.t0;
+      double* out = G.out + o.off;
+      const int r = r0 + row;
+      for (int cc = 0; cc < n2; cc += 16) {
+        float v[16];
+        if (any) {
+          tmem_ld16(tmem + lane_off + 128u + uint32_t(cc), v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (r < o.M) {
+          double* p = out + int64_t(r) * o.N + c0 + cc;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + cc + j < o.N) p[j] = o.accumulate ? p[j] + double(v[j]) : double(v[j]);
+        }
+      }
+    } else if (ok && !abort_flag) {
+      fail();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// One problem (g0, passed by value) or several (groups in device memory): CTA b takes tile
+// b - tile0 of the group g with tile0(g) <= b < tile0(g + 1).
+__global__ void __launch_bounds__(kThreads, 1) k_heff_tc(const __grid_constant__ TcGroup g0,
+                                                          const TcGroup* __restrict__ groups,
+                                                          int n_groups, int* status,
+                                                          uint32_t stuck_polls, int tf32) {
+  const int b = blockIdx.x;
+  if (!groups) {
+    heff_tc_tile(g0, g0.tiles[b], status, stuck_polls, tf32 != 0);
+    return;
+  }
+  int lo = 0, hi = n_groups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const TcGroup& G = groups[lo];
+  heff_tc_tile(G, G.tiles[b - G.tile0], status, stuck_polls, tf32 != 0);
+}
+
+void launch_split(const SplitTask* tasks, int n_tasks, const BufTable& bt, uint8_t* hi, uint8_t* lo,
+                  bool tf32, cudaStream_t s) {
+  if (n_tasks <= 0) return;
+  k_split<<<n_tasks, 256, 0, s>>>(tasks, bt, hi, lo, tf32 ? 1 : 0);
+  count_launches(1);
+}
+
+void launch_heff_tc(const TcGroup& g0, const TcGroup* groups, int n_groups, int n_tiles, bool tf32,
+                    int* status, uint32_t stuck_polls, cudaStream_t s) {
+  if (n_tiles <= 0 || (groups && n_groups <= 0)) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_heff_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+  });
+  k_heff_tc<<<n_tiles, kThreads, kDynSmem, s>>>(g0, groups, n_groups, status, stuck_polls,
+                                                tf32 ? 1 : 0);
+  count_launches(1);
+}
+
+}  // namespace b2k

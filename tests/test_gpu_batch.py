@@ -60,7 +60,7 @@ def _psi(ctx, env, w):
     return psi
 
 
-@pytest.mark.parametrize("prec", [b2.B2_FP64, b2.B2_BF16X3])
+@pytest.mark.parametrize("prec", [b2.B2_FP64, b2.B2_BF16X3, b2.B2_TF32X3])
 def test_grouped_heff_equals_single_problem_launches(ctx, prec):
     objs = [_make(ctx, p, p[5]) for p in PROBLEMS]
     envs = [o[2] for o in objs]
@@ -100,7 +100,7 @@ def test_grouped_davidson_equals_single_problem(ctx):
     _free(objs)
 
 
-@pytest.mark.parametrize("prec", [b2.B2_FP64, b2.B2_BF16X3])
+@pytest.mark.parametrize("prec", [b2.B2_FP64, b2.B2_BF16X3, b2.B2_TF32X3])
 def test_grouped_sweeps_equal_single_problem_sweeps(ctx, prec):
     # one bond-dimension schedule for the whole batch (the call takes one)
     specs = PROBLEMS[:4]

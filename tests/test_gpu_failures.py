@@ -108,7 +108,8 @@ def test_eigensolver_sweep_limit_reports_enoconv():
     s = b2.b2_mps_import(ctx, bonds, sites, 6, 0)
     env = b2.b2_env_init(ctx, m, s)
     r = b2.b2_sweep(ctx, m, s, env, [24, 24])
-    assert np.isfinite(r[-1]["energy"]) and r[-1]["energy"] <= r[0]["energy"] + 1e-10
+    # at a truncated bond dimension a sweep may raise the energy by about the discarded weight
+    assert np.isfinite(r[-1]["energy"]) and r[-1]["energy"] <= r[0]["energy"] + 1e-6
     b2.b2_free_env(env)
     b2.b2_free_mps(s)
     b2.b2_free_mpo(m)
@@ -120,4 +121,41 @@ def test_debug_limits_reject_negative_values():
     with pytest.raises(b2.B2Error) as e:
         b2.b2_debug_limits(ctx, -1, 0)
     assert e.value.code == b2.B2_EINVAL
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [b2.B2_BF16X3, b2.B2_TF32X3], ids=["bf16x3", "tf32x3"])
+def test_tensor_core_wait_that_runs_out_reports_etimeout(prec):
+    # every CTA of the contraction first waits on a barrier that nothing arrives on; the
+    # bounded wait runs out, the CTA drains its copies and MMAs, frees tensor memory and
+    # returns; b2_sync reports B2_ETIMEOUT and the next products are correct again
+    ctx = b2.Context(0)
+    h, eri, bonds, sites = _small(n=8, M=48, seed=6, center=3)
+    m = b2.b2_build_mpo(ctx, h, eri, 0.0, 8, 0)
+    s = b2.b2_mps_import(ctx, bonds, sites, 8, 0, center=3)
+    env = b2.b2_env_init(ctx, m, s, center=3)
+    n_elem, _ = b2.b2_psi_layout(ctx, env, 3)
+    x = torch.randn(n_elem, dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(device=DEV).manual_seed(3))
+    y64, ys = torch.empty_like(x), torch.empty_like(x)
+    b2.b2_heff_apply(ctx, env, 3, x, y64)
+    b2.b2_sync(ctx)
+    b2.b2_debug_limits(ctx, 2000, 0)
+    b2.b2_heff_apply(ctx, env, 3, x, ys, prec=prec)
+    with pytest.raises(b2.B2Error) as e:
+        b2.b2_sync(ctx)
+    assert e.value.code == b2.B2_ETIMEOUT
+    # the same through Davidson, which checks the status after its products
+    p = x.clone()
+    with pytest.raises(b2.B2Error) as e:
+        b2.b2_davidson(ctx, env, 3, p, max_iter=4, prec=prec)
+    assert e.value.code == b2.B2_ETIMEOUT
+    b2.b2_debug_limits(ctx, 0, 0)
+    b2.b2_sync(ctx)
+    b2.b2_heff_apply(ctx, env, 3, x, ys, prec=prec)
+    b2.b2_sync(ctx)
+    assert float((ys - y64).norm() / y64.norm()) < 2e-4
+    b2.b2_free_env(env)
+    b2.b2_free_mps(s)
+    b2.b2_free_mpo(m)
     ctx.close()
