@@ -313,11 +313,129 @@ struct RhoSector {
 };
 }  // namespace
 
+// Signature of a density-matrix sector: its quantum numbers and its parts with their
+// dimensions (the warm-start cache matches sectors on it).
+static std::vector<int64_t> rho_signature(const RhoSector& r) {
+  std::vector<int64_t> sig{r.q.key(), r.dim};
+  for (size_t a = 0; a < r.parts.size(); ++a) {
+    const int end = a + 1 < r.parts.size() ? r.part_off[a + 1] : r.dim;
+    sig.push_back((int64_t(r.parts[a].first) << 8) | r.parts[a].second);
+    sig.push_back(end - r.part_off[a]);
+  }
+  return sig;
+}
+
+// Eigen-decomposition of the sector density matrices rho into evals / evecs (layout of
+// secs), warm-started where the cache holds a basis of the same sector: rho' = V^T rho V,
+// Jacobi on rho' (eigenvectors W), evecs = V W.  The cache then holds evecs.
+static void eig_warm(Ctx* c, std::vector<RhoSector>& secs, DevBuf& rho, DevBuf& evals,
+                     DevBuf& evecs, RhoCache* cache, int* unconv) {
+  const int ns = int(secs.size());
+  std::vector<int> dims(ns);
+  std::vector<int64_t> offs(ns), eoffs(ns), warm(ns, -1);
+  int64_t tot = 0;
+  std::vector<std::vector<int64_t>> sigs(ns);
+  bool any_warm = false;
+  for (int j = 0; j < ns; ++j) {
+    dims[j] = secs[j].dim;
+    offs[j] = secs[j].off;
+    eoffs[j] = secs[j].eoff;
+    tot = std::max(tot, secs[j].off + int64_t(secs[j].dim) * secs[j].dim);
+    sigs[j] = rho_signature(secs[j]);
+    if (cache && cache->V.ptr) {
+      auto it = cache->by_sig.find(sigs[j]);
+      if (it != cache->by_sig.end() && it->second.second == dims[j] && dims[j] > 1) {
+        warm[j] = it->second.first;
+        any_warm = true;
+      }
+    }
+  }
+  double* flops_ctr = c->prof ? c->d_eig_flops : nullptr;
+  if (!any_warm) {
+    eigh_batched(c, dims, offs, eoffs, rho.as<double>(), evals.as<double>(), evecs.as<double>(),
+                 flops_ctr, unconv);
+  } else {
+    DevBuf rho2(c, sizeof(double) * std::max<int64_t>(tot, 1));
+    DevBuf W(c, sizeof(double) * std::max<int64_t>(tot, 1));
+    BufTable bt{};
+    bt.p[0] = rho.as<double>();
+    bt.p[1] = rho2.as<double>();
+    bt.p[2] = W.as<double>();
+    bt.p[3] = cache->V.as<double>();
+    bt.p[4] = evecs.as<double>();
+    GemmProgram p1, p2;
+    std::vector<b2k::CopyTask> cold_in;
+    for (int j = 0; j < ns; ++j) {
+      const int d = dims[j];
+      if (warm[j] < 0) {
+        cold_in.push_back({offs[j], offs[j], d, d, d, d, 0, 0, 1});
+        continue;
+      }
+      GemmTerm t{};
+      t.K1 = d;
+      t.alpha = 1.0;
+      // W = rho V
+      t.offP = offs[j]; t.bufP = 0; t.ldP = d;
+      t.offX = warm[j]; t.bufX = 3; t.ldX = d;
+      t.flags = kTwoOp;
+      p1.add_term(p1.add_out(2, offs[j], d, d, d, false), t);
+      // rho' = V^T W
+      t.offP = warm[j]; t.bufP = 3; t.ldP = d;
+      t.offX = offs[j]; t.bufX = 2; t.ldX = d;
+      t.flags = kTwoOp | kTransP;
+      p2.add_term(p2.add_out(1, offs[j], d, d, d, false), t);
+    }
+    p1.finalize(c);
+    p2.finalize(c);
+    p1.launch(c, bt);
+    p2.launch(c, bt);
+    DevBuf d_cin;
+    if (!cold_in.empty()) {
+      upload(c, d_cin, cold_in);
+      b2k::launch_copy(int(cold_in.size()), d_cin.as<b2k::CopyTask>(), bt, c->stream);
+    }
+    eigh_batched(c, dims, offs, eoffs, rho2.as<double>(), evals.as<double>(), W.as<double>(),
+                 flops_ctr, unconv);
+    // evecs = V W (warm sectors), W (cold sectors)
+    GemmProgram p3;
+    std::vector<b2k::CopyTask> cold_out;
+    for (int j = 0; j < ns; ++j) {
+      const int d = dims[j];
+      if (warm[j] < 0) {
+        cold_out.push_back({offs[j], offs[j], d, d, d, d, 0, 2, 4});
+        continue;
+      }
+      GemmTerm t{};
+      t.K1 = d;
+      t.alpha = 1.0;
+      t.offP = warm[j]; t.bufP = 3; t.ldP = d;
+      t.offX = offs[j]; t.bufX = 2; t.ldX = d;
+      t.flags = kTwoOp;
+      p3.add_term(p3.add_out(4, offs[j], d, d, d, false), t);
+    }
+    p3.finalize(c);
+    p3.launch(c, bt);
+    DevBuf d_cout;
+    if (!cold_out.empty()) {
+      upload(c, d_cout, cold_out);
+      b2k::launch_copy(int(cold_out.size()), d_cout.as<b2k::CopyTask>(), bt, c->stream);
+    }
+    B2_CUDA(cudaGetLastError());
+  }
+  if (cache) {
+    cache->by_sig.clear();
+    for (int j = 0; j < ns; ++j) cache->by_sig[sigs[j]] = {offs[j], dims[j]};
+    cache->V.reset(c, sizeof(double) * std::max<int64_t>(tot, 1));
+    B2_CUDA(cudaMemcpyAsync(cache->V.ptr, evecs.ptr, sizeof(double) * std::max<int64_t>(tot, 1),
+                            cudaMemcpyDeviceToDevice, c->stream));
+  }
+}
+
 // Batched eigen-decomposition of the sector density matrices, then the global selection.
 // Returns kept counts per sector (host) and the discarded weight.
 static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, DevBuf& rho,
                                        DevBuf& evals, DevBuf& evecs, int M, double cutoff,
-                                       double* discarded) {
+                                       double* discarded, RhoCache* cache = nullptr) {
   int ns = int(secs.size());
   std::vector<int> dims(ns), sec_of;
   std::vector<int64_t> offs(ns), eoffs(ns);
@@ -351,8 +469,7 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
     B2_CUDA(cudaEventRecord(e0, c->stream));
   }
   int* unconv = c->status() + 1;   // status word 1: Jacobi sweep limit reached
-  eigh_batched(c, dims, offs, eoffs, rho.as<double>(), evals.as<double>(), evecs.as<double>(),
-               c->prof ? c->d_eig_flops : nullptr, unconv);
+  eig_warm(c, secs, rho, evals, evecs, cache, unconv);
   if (c->prof) {
     B2_CUDA(cudaEventRecord(e1, c->stream));
     c->eig_events.push_back({e0, e1});
@@ -454,7 +571,8 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   prog.launch(c, bt);
   *flops += prog.flops;
   tr.mark("rho");
-  std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded);
+  std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded,
+                                         &env->rho_cache[2 * i]);
   tr.mark("eig+select");
 
   // new bond i+1 and A_i
@@ -637,7 +755,8 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   prog.launch(c, bt);
   *flops += prog.flops;
   tr.mark("rho");
-  std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded);
+  std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded,
+                                         &env->rho_cache[2 * i + 1]);
   tr.mark("eig+select");
 
   Bond nb;

@@ -201,6 +201,8 @@ struct b2_mpo_s {
   int n = 0, n_elec = 0, two_sz = 0;
   double e_core = 0.0;
   std::vector<int> D;                                // channels per bond
+  std::vector<int> chan_I, chan_H;                   // per bond: the "nothing applied yet" and
+                                                     // "whole term applied" channels (-1: none)
   std::vector<std::vector<int>> parity;              // per bond, per channel
   std::vector<std::vector<b2::QN>> dq;               // per bond, per channel (left part)
   struct Entry {

@@ -492,9 +492,38 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     int u, v;
     int pL;
     double coef;
+    bool block_h = false;
   };
   std::vector<Pending> pending;
   const int Da = mpo->D[i], Db = mpo->D[i + 2];
+  // The two block-Hamiltonian terms, L_H (x) 1 (x) R_H (left block's Hamiltonian, right
+  // block's identity) and L_I (x) 1 (x) R_I (the reverse), carry the energy scale of H_eff;
+  // they are kept out of the precombination as terms of their own (flag kBlockH) so that the
+  // split-precision path can evaluate them in FP64 (normal-ordering idea of Sec. 2.1.5: the
+  // low-precision products then carry only the coupling between the blocks and the sites).
+  std::vector<std::vector<Edge>> block_h_edges(16);   // kept for the diagonal
+  for (int v = 0; v < 16; ++v) {
+    auto& edges = pat[v * 16 + v];
+    for (int which = 0; which < 2; ++which) {
+      const int a = which ? mpo->chan_H[i] : mpo->chan_I[i];
+      const int b = which ? mpo->chan_H[i + 2] : mpo->chan_I[i + 2];
+      if (a < 0 || b < 0) continue;
+      for (size_t k = 0; k < edges.size(); ++k)
+        if (edges[k].a == a && edges[k].b == b) {
+          Pending p;
+          p.u = p.v = v;
+          p.lop = combL.make(L, 2, {{a, edges[k].v}});
+          p.rop = combR.make(R, 3, {{b, 1.0}});
+          p.pL = mpo->parity[i][a];
+          p.coef = p.lop.coef * p.rop.coef;
+          p.block_h = true;
+          pending.push_back(std::move(p));
+          block_h_edges[v].push_back(edges[k]);
+          edges.erase(edges.begin() + k);
+          break;
+        }
+    }
+  }
   std::vector<int> dega(Da, 0), degb(Db, 0), posa(Da, -1), posb(Db, -1);
   for (int pv = 0; pv < 256; ++pv) {
     auto& edges = pat[pv];
@@ -595,7 +624,7 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
       t.offQ = p.rop.off[in.jr]; t.bufQ = p.rop.buf; t.ldQ = in.mr;    // R [m_r' x m_r]
       t.K1 = in.ml;
       t.K2 = in.mr;
-      t.flags = kTransQ;
+      t.flags = kTransQ | (p.block_h ? b2k::kBlockH : uint8_t(0));
       t.alpha = p.coef * sign;
       prog.add_term(ob, t);
     }
@@ -631,6 +660,8 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
 
   // diagonal: diagonal patterns whose channels keep the sector (dq = 0 on both sides)
   std::vector<std::vector<Edge>> dedges(16);
+  for (int v = 0; v < 16; ++v)
+    for (const auto& e : block_h_edges[v]) dedges[v].push_back(e);
   for (int v = 0; v < 16; ++v)
     for (const auto& e : pat[v * 16 + v])
       if (mpo->dq[i][e.a] == QN{0, 0} && mpo->dq[i + 2][e.b] == QN{0, 0}) dedges[v].push_back(e);
@@ -671,10 +702,13 @@ namespace {
 inline int pad16(int x) { return (x + 15) & ~15; }
 inline int elem_bytes(b2_prec p) { return p == B2_TF32X3 ? 4 : 2; }
 
-// Host tables of the tensor-core form of the window's contraction (see TcProgram).
-void build_tc(WindowProgram& wp) {
+// Host tables of the tensor-core form of the window's contraction (see TcProgram): the
+// block-Hamiltonian terms go to an FP64 program that overwrites every output, the others
+// to the tensor-core tables, whose outputs then accumulate.
+void build_tc(Ctx* c, WindowProgram& wp) {
   TcProgram& tp = wp.tc;
   const GemmProgram& g = wp.heff;
+  for (const auto& o : g.outs) tp.block_h.add_out(o.buf, o.off, o.M, o.N, o.ld, false);
   std::map<std::pair<int, int64_t>, int64_t> env_dst;
   auto env_operand = [&](int buf, int64_t off, int rows, int cols, int ld) -> int64_t {
     B2_REQUIRE(ld == cols, B2_EINVAL, "internal: operand block not contiguous");
@@ -703,12 +737,17 @@ void build_tc(WindowProgram& wp) {
     to.off = o.off;
     to.M = o.M;
     to.N = o.N;
-    to.accumulate = o.accumulate;
+    to.accumulate = 1;
     to.t0 = int(tp.terms.size());
-    double c = 0;
+    double cst = 0;
     for (int t = o.t0; t < o.t1; ++t) {
       const GemmTerm& gt = g.terms[t];
-      B2_REQUIRE(gt.flags == kTransQ && gt.bufX == 0, B2_EINVAL, "internal: H_eff term form");
+      B2_REQUIRE((gt.flags & ~b2k::kBlockH) == kTransQ && gt.bufX == 0 && !o.accumulate,
+                 B2_EINVAL, "internal: H_eff term form");
+      if (gt.flags & b2k::kBlockH) {
+        tp.block_h.add_term(int(i), gt);
+        continue;
+      }
       auto ip = psi_dst.find(gt.offX);
       B2_REQUIRE(ip != psi_dst.end(), B2_EINVAL, "internal: psi block of a term");
       b2k::TcTerm tt{};
@@ -719,16 +758,18 @@ void build_tc(WindowProgram& wp) {
       tt.K2 = gt.K2;
       tt.alpha = static_cast<float>(gt.alpha);
       tp.terms.push_back(tt);
-      c += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
+      cst += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
     }
     to.t1 = int(tp.terms.size());
     tp.outs.push_back(to);
+    if (to.t1 == to.t0) continue;   // nothing to add to the block-Hamiltonian part
     for (int r = 0; r < o.M; r += 128)
       for (int cc = 0; cc < o.N; cc += 128) {
         tp.tiles.push_back({int(i), r, cc});
-        cost.push_back(c);
+        cost.push_back(cst);
       }
   }
+  tp.block_h.finalize(c);
   // most expensive tiles first
   std::vector<int> order(tp.tiles.size());
   for (size_t k = 0; k < order.size(); ++k) order[k] = int(k);
@@ -793,7 +834,7 @@ TcProgram& tc_program(b2_env_s* env, int site, b2_prec prec) {
   Ctx* c = env->ctx;
   TcProgram& tp = wp.tc;
   if (!tp.built) {
-    build_tc(wp);
+    build_tc(c, wp);
     upload(c, tp.d_outs, tp.outs);
     upload(c, tp.d_terms, tp.terms);
     upload(c, tp.d_tiles, tp.tiles);
@@ -831,6 +872,7 @@ void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double 
   if (!tp) {
     wp.heff.launch(c, bt);
   } else {
+    tp->block_h.launch(c, bt);   // FP64 block-Hamiltonian terms write the output
     b2k::launch_heff_tc(tc_group(*tp, prec, out), nullptr, 1, int(tp->tiles.size()),
                         prec == B2_TF32X3, c->status(), c->stuck_polls, c->stream);
     B2_CUDA(cudaGetLastError());
@@ -870,6 +912,7 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
     } else {
       TcProgram& tp = tc_program(env, site, prec);
       split_psi(c, tp, psis[i], prec);
+      tp.block_h.launch(c, bt);   // FP64 block-Hamiltonian terms write the output
       b2k::TcGroup g = tc_group(tp, prec, outs[i]);
       g.tile0 = tiles;
       groups_tc.push_back(g);

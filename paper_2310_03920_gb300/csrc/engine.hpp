@@ -70,6 +70,7 @@ struct PsiLayout {
 // psi^T once per product) and the split planes ([hi | lo], elements * element size each).
 struct TcProgram {
   bool built = false;
+  GemmProgram block_h;   // FP64: the block-Hamiltonian terms (kBlockH), written first
   std::vector<b2k::TcOut> outs;
   std::vector<b2k::TcTerm> terms;
   std::vector<b2k::TcTile> tiles;
@@ -94,6 +95,17 @@ struct WindowProgram {
   TcProgram tc;
 };
 
+// Eigenvectors of the density-matrix sectors of the last split at one window and
+// direction, kept to warm-start the next sweep's eigensolver there: a sector whose
+// composition is unchanged (same quantum numbers, same contributing (sector, site state)
+// parts of the same dimensions) is first rotated into this basis, rho' = V^T rho V, which
+// near convergence is almost diagonal, so Jacobi needs a few sweeps instead of ~20.  Any
+// orthogonal V gives the same eigen-decomposition; the cache only changes the work.
+struct RhoCache {
+  std::map<std::vector<int64_t>, std::pair<int64_t, int>> by_sig;   // signature -> (offset, dim)
+  DevBuf V;
+};
+
 }  // namespace b2
 
 struct b2_env_s {
@@ -102,6 +114,7 @@ struct b2_env_s {
   b2_mps_s* mps = nullptr;
   std::vector<b2::EnvBond> L, R;   // per bond
   std::map<int, std::unique_ptr<b2::WindowProgram>> windows;
+  std::map<int, b2::RhoCache> rho_cache;   // key: 2 * window + (1 for the backward split)
   int version_counter = 0;
 };
 

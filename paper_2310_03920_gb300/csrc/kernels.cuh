@@ -22,7 +22,9 @@ struct BufTable {
 //   2-operand (flags & kTwoOp): out += alpha * op(P) [M x K1] * op(X) [K1 x N]
 // op(P) = P^T when flags & kTransP, op(Q) = Q^T when flags & kTransQ (2-operand: op(X) =
 // X^T when flags & kTransQ).  Matrices are row-major with leading dimensions ld*.
-enum : uint8_t { kTransP = 1, kTransQ = 2, kTwoOp = 4 };
+// kBlockH marks the two block-Hamiltonian terms of an H_eff output (L_H (x) 1 (x) R_H and
+// L_I (x) 1 (x) R_I: the energy scale of the product); the kernels ignore it.
+enum : uint8_t { kTransP = 1, kTransQ = 2, kTwoOp = 4, kBlockH = 8 };
 struct GemmTerm {
   int64_t offP, offX, offQ;
   int ldP, ldX, ldQ;

@@ -339,6 +339,10 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
   mpo->D.resize(n + 1);
   mpo->parity.resize(n + 1);
   mpo->dq.resize(n + 1);
+  mpo->chan_I.assign(n + 1, -1);
+  mpo->chan_H.assign(n + 1, -1);
+  for (int k = 0; k < n; ++k) mpo->chan_I[k] = chans[k].get(kTypeI);
+  for (int k = 1; k <= n; ++k) mpo->chan_H[k] = chans[k].get(kTypeH);
   for (int k = 0; k <= n; ++k) {
     int d = int(chans[k].keys.size());
     mpo->D[k] = d;

@@ -47,8 +47,13 @@ constexpr int kQBytes = 64 * 128;                    // <= 64 rows (one T chunk 
 constexpr int kStageBytes = 2 * kPBytes + 2 * kQBytes;
 constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo
 constexpr int kDynSmem = kStages * kStageBytes + 2 * kTpBytes + 1024;
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 256;                       // T0 [0,64), T1 [64,128), acc [128,256)
+constexpr int kThreads = 320;                        // producer, MMA, 8 converter warps
+constexpr int kConv = 256;                           // converter threads
+// TMEM columns: T0 [0,64), T1 [64,128), acc0 [128,256), acc1 [256,384)
+constexpr int kTmemCols = 512;
+// chain units summed in one FP32 accumulator before it is added to the FP64 output: bounds
+// the FP32 rounding error of the long term sums (thousands of terms per output block)
+constexpr int kGroup = 16;
 constexpr uint32_t kDefaultWait = 1u << 22;
 constexpr uint32_t kDrainWait = 1u << 22;
 
@@ -141,6 +146,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
           dst),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -245,7 +262,8 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
                                              uint32_t stuck_polls, bool tf32) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  __shared__ __align__(8) uint64_t tfull[2], tempty[2], tpready[2], tpempty[2], accb, drainb;
+  __shared__ __align__(8) uint64_t tfull[2], tempty[2], tpready[2], tpempty[2], drainb;
+  __shared__ __align__(8) uint64_t accfull[2], accempty[2];
   __shared__ __align__(8) uint64_t neverb;   // nothing arrives on it (failure-path tests)
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -272,11 +290,12 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     }
     for (int b = 0; b < 2; ++b) {
       bar_init(&tfull[b], 1);
-      bar_init(&tempty[b], 128);
-      bar_init(&tpready[b], 128);
+      bar_init(&tempty[b], kConv);
+      bar_init(&tpready[b], kConv);
       bar_init(&tpempty[b], 1);
+      bar_init(&accfull[b], 1);
+      bar_init(&accempty[b], kConv);
     }
-    bar_init(&accb, 1);
     bar_init(&drainb, 1);
     bar_init(&neverb, 1);
     abort_flag = 0;
@@ -381,8 +400,8 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t item = 0;
-      bool ok = true, started = false;
-      const uint32_t t_base = tmem, acc_tm = tmem + 128;
+      bool ok = true;
+      const uint32_t t_base = tmem;
       const uint32_t id2 = idesc(n2, tf32);
       auto take = [&](int& s) -> bool {
         s = int(item % kStages);
@@ -424,8 +443,18 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         commit(&tfull[b]);
         return true;
       };
-      auto mma2 = [&](const Unit& u, uint32_t idx) -> bool {
+      // MMA2 of unit idx into accumulator (idx / kGroup) & 1; the first unit of a group
+      // overwrites it (after the converter has added the group two back to the output),
+      // the last one signals it full
+      auto mma2 = [&](const Unit& u, uint32_t idx, bool last) -> bool {
         const int b = idx & 1;
+        const uint32_t g = idx / kGroup;
+        const int ab = int(g & 1);
+        const bool gstart = (idx % kGroup) == 0;
+        if (gstart && g >= 2 && !bar_wait(&accempty[ab], ((g >> 1) & 1) ^ 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          return false;
+        }
         if (!bar_wait(&tpready[b], (idx >> 1) & 1, limit, &abort_flag)) {
           if (!abort_flag) fail();
           return false;
@@ -439,16 +468,17 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         const uint32_t st = smem_u32(stage_mem + s * kStageBytes);
         const uint32_t tpH = smem_u32(tp_mem + b * kTpBytes), tpL = tpH + kPBytes;
         const uint32_t sbo = uint32_t(kg) * 128;
+        const uint32_t acc_tm = tmem + 128u + uint32_t(ab) * 128u;
         for (int ks = 0; ks < ksteps; ++ks) {
           const uint32_t off = uint32_t(ks) * 256;
           mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + off, sbo), id2,
-              (started || ks > 0) ? 1u : 0u);
+              (!gstart || ks > 0) ? 1u : 0u);
           mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + kPBytes + off, sbo), id2, 1u);
           mma(tf32, acc_tm, sdesc(tpL + off, 1024), sdesc(st + off, sbo), id2, 1u);
         }
-        started = true;
         commit(&empty[s]);
         commit(&tpempty[b]);
+        if (last || idx % kGroup == kGroup - 1) commit(&accfull[ab]);
         ++item;
         return true;
       };
@@ -469,25 +499,56 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
           next(ux);
           if (!ok) break;
         }
-        ok = mma2(uy, iy++);
-        next(uy);
+        Unit un = uy;
+        next(un);
+        ok = mma2(uy, iy++, un.t >= o.t1);
+        uy = un;
       }
-      // accumulator complete (also with no MMA at all); then every MMA issued has finished
-      commit(&accb);
+      // every MMA issued has finished before TMEM is freed
       commit(&drainb);
       if (!bar_drain(&drainb, 0)) fail();
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ converter and epilogue
-    const int quad = warp & 3;              // TMEM lane quarter of this warp
+    // ------------------------------------------------------------ converter and flushes
+    // 8 warps: warp w reads TMEM lane quarter w % 4 (tile rows), the two warps of a quarter
+    // take the two halves of the columns
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;       // tile row = TMEM lane
     const uint32_t lane_off = uint32_t(quad * 32) << 16;
+    const int hw = wk / 2;                  // T columns per half (32 bf16, 16 tf32)
+    const uint32_t rbase = uint32_t(row >> 3) * 1024 + uint32_t(row & 7) * 16;
+    double* out = G.out + o.off;
+    const int r = r0 + row;
+    bool ok = true;
+    // add accumulator group g to the FP64 output; every decision is uniform over the warp
+    // (__all_sync) so that the warp-collective TMEM loads never run in part of a warp
+    auto flush = [&](uint32_t g) -> bool {
+      const int ab = int(g & 1);
+      if (!__all_sync(0xffffffffu, bar_wait(&accfull[ab], (g >> 1) & 1, limit, &abort_flag))) {
+        if (!abort_flag) fail();
+        return false;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[64];
+      const int cb = half * 64;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (cb + 16 * j < n2) tmem_ld16_async(tmem + lane_off + 128u + uint32_t(ab) * 128u + uint32_t(cb + 16 * j), v + 16 * j);
+      tmem_wait_ld();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(&accempty[ab]);
+      if (r < o.M) {
+        double* p = out + int64_t(r) * o.N + c0 + cb;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+          if (cb + j < n2 && c0 + cb + j < o.N) p[j] += double(__uint_as_float(v[j]));
+      }
+      return true;
+    };
     Unit u = first;
     uint32_t idx = 0;
-    bool ok = true;
-    // every decision is made uniform over the warp (__all_sync) so that the warp-collective
-    // TMEM loads never run in part of a warp
     while (u.t < o.t1) {
       const int b = idx & 1;
       bool w = bar_wait(&tfull[b], (idx >> 1) & 1, limit, &abort_flag);
@@ -501,18 +562,26 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       const TcTerm tm = G.terms[u.t];
       const float alpha = tm.alpha;
       const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
+      const int cb = half * hw;
       unsigned char* tpH = tp_mem + b * kTpBytes;
       unsigned char* tpL = tpH + kPBytes;
-      const uint32_t rbase = uint32_t(row >> 3) * 1024 + uint32_t(row & 7) * 16;
-      for (int cc = 0; cc < n1; cc += 16) {
-        float v[16];
-        tmem_ld16(tmem + lane_off + uint32_t(b * 64 + cc), v);
+      uint32_t v[32];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (16 * j < hw && cb + 16 * j < n1) tmem_ld16_async(tmem + lane_off + uint32_t(b * 64 + cb + 16 * j), v + 16 * j);
+      tmem_wait_ld();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(&tempty[b]);   // T of this buffer is in registers
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int cc = cb + 16 * j;
+        if (16 * j >= hw || cc >= n1) continue;
         if (tf32) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {   // 4 k-groups of 4 elements
             uint32_t hh[4], ll[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) split_tf32(alpha * v[4 * q + e], hh[e], ll[e]);
+            for (int e = 0; e < 4; ++e) split_tf32(alpha * __uint_as_float(v[16 * j + 4 * q + e]), hh[e], ll[e]);
             const uint32_t off = rbase + uint32_t((cc >> 2) + q) * 128;
             *reinterpret_cast<uint4*>(tpH + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
             *reinterpret_cast<uint4*>(tpL + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
@@ -522,7 +591,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
           for (int q = 0; q < 2; ++q) {   // 2 k-groups of 8 elements
             uint16_t hh[8], ll[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) split_bf16(alpha * v[8 * q + e], hh[e], ll[e]);
+            for (int e = 0; e < 8; ++e) split_bf16(alpha * __uint_as_float(v[16 * j + 8 * q + e]), hh[e], ll[e]);
             const uint32_t off = rbase + uint32_t((cc >> 3) + q) * 128;
             *reinterpret_cast<uint4*>(tpH + off) =
                 make_uint4(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16),
@@ -533,37 +602,17 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
           }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      bar_arrive(&tempty[b]);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(&tpready[b]);
+      // the group before this one is complete once this unit's T' is handed over
+      if (idx % kGroup == 0 && idx > 0 && !flush(idx / kGroup - 1)) {
+        ok = false;
+        break;
+      }
       next(u);
       ++idx;
     }
-    const bool acc_ready = ok && __all_sync(0xffffffffu, bar_wait(&accb, 0, limit, &abort_flag));
-    if (acc_ready) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const bool any = o.t1 > o.t0;
-      double* out = G.out + o.off;
-      const int r = r0 + row;
-      for (int cc = 0; cc < n2; cc += 16) {
-        float v[16];
-        if (any) {
-          tmem_ld16(tmem + lane_off + 128u + uint32_t(cc), v);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        }
-        if (r < o.M) {
-          double* p = out + int64_t(r) * o.N + c0 + cc;
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + cc + j < o.N) p[j] = o.accumulate ? p[j] + double(v[j]) : double(v[j]);
-        }
-      }
-    } else if (ok && !abort_flag) {
-      fail();
-    }
+    if (ok && idx > 0 && !flush((idx - 1) / kGroup)) ok = false;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
