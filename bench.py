@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the split-precision sweep compared with FP64 on the same state")
+                    help="skip the split-precision sweeps compared with FP64 on the same state")
+    ap.add_argument("--no-window", action="store_true",
+                    help="skip the n=36 middle-window leg (products at M=1000/2000, Davidson "
+                         "at M=1000 in FP64 and in split precision)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "window_M1000", "window_M2000", "batch64", "grad_n24",
@@ -174,10 +177,11 @@ def measured_peaks(torch):
     return peaks
 
 
-def oracle_sample(budget_s, n_threads=None):
+def oracle_sample(budget_s):
     """The CPU oracle on a bounded sample of the workload: H_eff . psi products at the
-    middle window (sites 15, 16) of the same random MPS.  Returns (seconds per product,
-    number of products, setup seconds)."""
+    middle window (sites 15, 16) of the workload's random MPS centred there, and the
+    algorithmic flops of one product counted by the oracle itself (block-sparse form of its
+    own term list).  Returns (seconds per product, products, setup seconds, flops)."""
     import numpy as np
     from oracle import dmrg, mpo
     h, eri, bonds, sites = workload_inputs()
@@ -188,6 +192,7 @@ def oracle_sample(budget_s, n_threads=None):
     d = dmrg.DMRG(mpo.MPO(h, eri), bonds, sites_c, center=c)
     H = d.heff(c)
     setup = time.perf_counter() - t0
+    flops = H.algorithmic_flops(d.lab[c], d.lab[c + 2])
     x = d.psi
     times = []
     t_start = time.perf_counter()
@@ -198,23 +203,38 @@ def oracle_sample(budget_s, n_threads=None):
         times.append(time.perf_counter() - t1)
         if time.perf_counter() - t_start > budget_s or len(times) >= 50:
             break
-    return statistics.median(times), len(times), setup, bonds, sites_c, c, h, eri
+    return statistics.median(times), len(times), setup, flops
 
 
-def middle_window_flops(b2, ctx, h, eri, bonds, sites_c, c):
-    """Algorithmic flops of one H_eff . psi at the oracle sample's window (library count)."""
-    import torch
+def gpu_middle_window_product(b2, torch, ctx):
+    """The same sample on the GPU: FP64 H_eff . psi products at window (15, 16) of the
+    workload's random MPS centred there (the oracle sample's input), timed with CUDA events
+    on the context stream.  Returns (ms per product, library flops, oracle-definition
+    flops are not computed here)."""
+    from synth import random_mps
+    h, eri, bonds, sites = workload_inputs()
+    c = WORKLOAD["L"] // 2 - 1
+    sites_c = random_mps(bonds, seed=WORKLOAD["mps_seed"], center=c)
     m = b2.b2_build_mpo(ctx, h, eri, 0.0, WORKLOAD["L"], 0)
     s = b2.b2_mps_import(ctx, bonds, sites_c, WORKLOAD["L"], 0, center=c)
     env = b2.b2_env_init(ctx, m, s, center=c)
     n_elem, _ = b2.b2_psi_layout(ctx, env, c)
-    x = torch.ones(n_elem, dtype=torch.float64, device="cuda")
+    x = torch.empty(n_elem, dtype=torch.float64, device="cuda")
+    b2.b2_psi_from_mps(ctx, env, c, x)
     y = torch.empty_like(x)
     fl = b2.b2_heff_apply(ctx, env, c, x, y)
+    torch.cuda.synchronize()
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        b2.b2_heff_apply(ctx, env, c, x, y)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
     b2.b2_free_env(env)
     b2.b2_free_mps(s)
     b2.b2_free_mpo(m)
-    return fl
+    return e0.elapsed_time(e1) / reps, fl
 
 
 def cpu_cores():
@@ -231,19 +251,14 @@ def cpu_cores():
 
 def run_reference(args):
     """The oracle as the reference arm: each step is a bounded sample of the workload
-    (H_eff . psi products at the middle window, timed on the host cores).  The flop count
-    of one product is the library's count for the same window, the unit of the main arm."""
+    (H_eff . psi products at the middle window, timed on the host cores); the flops of one
+    product are counted by the oracle (block-sparse form of its own term list).  Nothing of
+    the GPU library is loaded."""
     rank, world, local = dist_info()
     if rank != 0:
         return
     budget = max(2.0, args.cpu_budget)
-    sec, nprod, setup, bonds, sites_c, c, h, eri = oracle_sample(budget)
-    import torch
-    torch.cuda.set_device(local)
-    from paper_2310_03920_gb300 import b2
-    ctx = b2.Context(local)
-    fl = middle_window_flops(b2, ctx, h, eri, bonds, sites_c, c)
-    ctx.close()
+    sec, nprod, setup, fl = oracle_sample(budget)
     value = fl / sec / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -253,101 +268,113 @@ def run_reference(args):
                        "M": WORKLOAD["M"], "sample": "H_eff.psi at the middle window"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
                              "kind": "oracle",
-                             "sample": "%d oracle H_eff.psi products at window %d (setup %.1f s)"
-                                       % (nprod, c, setup)},
+                             "sample": "%d oracle H_eff.psi products at window %d of the "
+                                       "workload's random MPS (setup %.1f s); %.4g flops per "
+                                       "product (oracle count)" % (nprod, WORKLOAD["L"] // 2 - 1,
+                                                                   setup, fl)},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_window(args):
+def window_leg(b2, torch, ctx, M, davidson, reps, peaks):
     """Middle window (sites 17, 18) of the n = 36, N = 36 ab initio system (60 Cholesky
-    vectors decaying as exp(-|p-q|/6), seed 2) at M = 1000 or 2000 from a random MPS
-    centred there.  Times single H_eff . psi products in FP64 and in split precision
-    (bf16 x3) and their relative difference; with --davidson also the window solve in split
-    precision with FP64 refinement to |r|^2 <= 1e-7, an FP64 solve started from its vector,
-    and |dE| between the two."""
-    import torch
-    from paper_2310_03920_gb300 import b2
+    vectors decaying as exp(-|p-q|/6), seed 2) at bond dimension M from a random MPS centred
+    there.  Times single H_eff . psi products in FP64, bf16 x3 and tf32 x3 (CUDA events on
+    the context stream, L2 flushed before each timing) and their relative difference to
+    FP64.  With davidson: the window's ground state from a common start vector (an FP64
+    Davidson to |r|^2 <= 1e-5 from the MPS's psi, untimed) to |r|^2 <= 1e-10 in FP64 and
+    with split products refined in FP64, with times, products and |dE|."""
     from synth import config_integrals, occupancies, random_mps, sector_sizes
-    M = 1000 if args.workload == "window_M1000" else 2000
     h, eri, N, tsz, kind = config_integrals("abinitio_n36")
     n = h.shape[0]
     c = n // 2 - 1
     t0 = time.perf_counter()
     bonds = sector_sizes(n, N, tsz, M, occupancies(n, N, kind))
     sites = random_mps(bonds, seed=2 + 100, center=c)
-    t_gen = time.perf_counter() - t0
-    ctx = b2.Context(0)
-    t0 = time.perf_counter()
     mpo_h = b2.b2_build_mpo(ctx, h, eri, 0.0, N, tsz)
-    t_mpo = time.perf_counter() - t0
     mps_h = b2.b2_mps_import(ctx, bonds, sites, N, tsz, center=c)
-    t0 = time.perf_counter()
     env = b2.b2_env_init(ctx, mpo_h, mps_h, center=c)
-    t_env = time.perf_counter() - t0
+    setup = time.perf_counter() - t0
     n_elem, n_blk = b2.b2_psi_layout(ctx, env, c)
     psi0 = torch.empty(n_elem, dtype=torch.float64, device="cuda")
     b2.b2_psi_from_mps(ctx, env, c, psi0)
-    y = torch.empty_like(psi0)
-
-    def time_products(prec, reps):
-        b2.b2_heff_apply(ctx, env, c, psi0, y, prec=prec)       # builds / precombines once
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fl = b2.b2_heff_apply(ctx, env, c, psi0, y, prec=prec)
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps, fl
-
-    ms64, fl = time_products(b2.B2_FP64, 2)
-    y64 = y.clone()
-    ms16, _ = time_products(b2.B2_BF16X3, max(3, args.steps))
-    rel = float((y - y64).norm() / y64.norm())
-    res = None
-    if args.davidson:
-        # mixed-precision solve to |r_FP64|^2 <= tol, then an FP64 solve started from its
-        # vector to the same tolerance: |dE| between the two converged energies
-        tol = 1e-7
-        res = {"conv_tol": tol}
-        p = psi0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e16, n16, r16 = b2.b2_davidson(ctx, env, c, p, max_iter=60, max_subspace=40,
-                                       conv_tol=tol, prec=b2.B2_BF16X3, refine_max=12)
-        torch.cuda.synchronize()
-        res["bf16x3"] = {"energy": e16, "n_matvec": n16, "resid2": r16,
-                         "seconds": time.perf_counter() - t0}
-        t0 = time.perf_counter()
-        e64, n64, r64 = b2.b2_davidson(ctx, env, c, p, max_iter=60, max_subspace=40,
-                                       conv_tol=tol, prec=b2.B2_FP64)
-        torch.cuda.synchronize()
-        res["fp64_from_mixed"] = {"energy": e64, "n_matvec": n64, "resid2": r64,
-                                  "seconds": time.perf_counter() - t0}
-        res["dE"] = abs(e16 - e64)
-    peaks = measured_peaks(torch)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res = {"config": {"n": n, "n_elec": N, "M": M, "window": [c, c + 1], "psi_elements": n_elem,
+                      "psi_blocks": n_blk}, "setup_s": setup}
     bf16_peak = peaks.get("bf16_tflops", 1887.4)
-    line = {"metric": METRIC, "value": fl / (ms16 * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": 1, "ms_per_step": ms16, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
-            "config": {"workload": "abinitio_n36_N36_M%d_middle_window" % M, "n": n, "n_elec": N,
-                       "M": M, "window": [c, c + 1], "psi_elements": n_elem, "psi_blocks": n_blk,
-                       "l2": "inputs larger than L2 (environments)"},
-            "heff": {"algo_flops": fl, "fp64_ms": ms64, "bf16x3_ms": ms16,
-                     "fp64_tflops": fl / (ms64 * 1e-3) / 1e12,
-                     "bf16x3_effective_tflops": fl / (ms16 * 1e-3) / 1e12,
-                     "bf16x3_tensor_pipe_tflops": 3 * fl / (ms16 * 1e-3) / 1e12,
-                     "bf16x3_frac_of_measured_bf16": 3 * fl / (ms16 * 1e-3) / 1e12 / bf16_peak,
-                     "bf16x3_rel_error": rel, "speedup": ms64 / ms16},
-            "setup_s": {"inputs": t_gen, "mpo": t_mpo, "env_init": t_env}}
-    if res is not None:
-        line["davidson"] = res
-    print(json.dumps(line), flush=True)
+    ys = {}
+    for name, prec in (("fp64", b2.B2_FP64), ("bf16x3", b2.B2_BF16X3), ("tf32x3", b2.B2_TF32X3)):
+        y = torch.empty_like(psi0)
+        fl = b2.b2_heff_apply(ctx, env, c, psi0, y, prec=prec)   # builds / splits once
+        ms = []
+        for _ in range(1 if prec == b2.B2_FP64 else reps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            b2.b2_heff_apply(ctx, env, c, psi0, y, prec=prec)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        ys[name] = y
+        r = {"ms": t, "algo_flops": fl, "effective_tflops": fl / (t * 1e-3) / 1e12}
+        if prec != b2.B2_FP64:
+            pipe = 3 * fl / (t * 1e-3) / 1e12
+            peak = bf16_peak if prec == b2.B2_BF16X3 else bf16_peak / 2   # tf32: half the rate
+            r.update({"tensor_pipe_tflops": pipe, "tensor_peak_tflops": peak,
+                      "tensor_frac": pipe / peak,
+                      "rel_err_vs_fp64": float((y - ys["fp64"]).norm() / ys["fp64"].norm()),
+                      "speedup_vs_fp64": res["fp64"]["ms"] / t})
+        res[name] = r
+    if davidson:
+        p = psi0.clone()
+        b2.b2_davidson(ctx, env, c, p, max_iter=200, max_subspace=40, conv_tol=1e-5)
+        dav = {"conv_tol": 1e-10, "start": "FP64 Davidson to |r|^2 <= 1e-5 from the MPS's psi"}
+        for name, prec in (("fp64", b2.B2_FP64), ("tf32x3", b2.B2_TF32X3), ("bf16x3", b2.B2_BF16X3)):
+            q = p.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e, nmv, r2 = b2.b2_davidson(ctx, env, c, q, max_iter=200, max_subspace=40,
+                                        conv_tol=1e-10, prec=prec, refine_max=20)
+            torch.cuda.synchronize()
+            dav[name] = {"seconds": time.perf_counter() - t0, "energy": e, "n_matvec": nmv,
+                         "resid2": r2}
+        for name in ("tf32x3", "bf16x3"):
+            dav[name]["dE_vs_fp64"] = abs(dav[name]["energy"] - dav["fp64"]["energy"])
+            dav[name]["speedup_vs_fp64"] = dav["fp64"]["seconds"] / dav[name]["seconds"]
+        res["davidson"] = dav
+    del flush
     b2.b2_free_env(env)
     b2.b2_free_mps(mps_h)
     b2.b2_free_mpo(mpo_h)
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_window(args):
+    """Middle window of the n = 36 ab initio system at M = 1000 or 2000 (window_leg): the
+    split-precision product is the line's value; with --davidson also the window solves."""
+    import torch
+    from paper_2310_03920_gb300 import b2
+    M = 1000 if args.workload == "window_M1000" else 2000
+    ctx = b2.Context(0)
+    peaks = measured_peaks(torch)
+    b2.b2_profile(ctx, True)
+    with ClockSampler(0) as clk:
+        res = window_leg(b2, torch, ctx, M, args.davidson, max(3, args.steps), peaks)
+    prof = b2.b2_profile_read(ctx)
+    b2.b2_profile(ctx, False)
+    best = max(("bf16x3", "tf32x3"), key=lambda k: res[k]["effective_tflops"])
+    line = {"metric": METRIC, "value": res[best]["effective_tflops"], "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": max(3, args.steps), "warmup": 1, "ms_per_step": res[best]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": best,
+            "data": "synthetic",
+            "config": dict(workload="abinitio_n36_N36_M%d_middle_window" % M,
+                           l2="flushed before each product (256 MB write)", **res["config"]),
+            "window": res, "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -654,7 +681,7 @@ def main():
     mixed = None
     if args.prec == "fp64" and not args.no_mixed:
         mixed = {}
-        for name, pr in (("fp64", b2.B2_FP64), ("bf16x3", b2.B2_BF16X3)):
+        for name, pr in (("fp64", b2.B2_FP64), ("bf16x3", b2.B2_BF16X3), ("tf32x3", b2.B2_TF32X3)):
             s3 = b2.b2_mps_import(ctx, bonds_now, sites_now, L, 0, center=0)
             en3 = b2.b2_env_init(ctx, mpo_h, s3, center=0)
             torch.cuda.synchronize()
@@ -665,8 +692,9 @@ def main():
                            "energy": r3[0]["energy"], "n_matvec": r3[0]["n_matvec"]}
             b2.b2_free_env(en3)
             b2.b2_free_mps(s3)
-        mixed["dE"] = abs(mixed["bf16x3"]["energy"] - mixed["fp64"]["energy"])
-        mixed["speedup"] = mixed["fp64"]["sweep_ms"] / mixed["bf16x3"]["sweep_ms"]
+        for name in ("bf16x3", "tf32x3"):
+            mixed[name]["dE_vs_fp64"] = abs(mixed[name]["energy"] - mixed["fp64"]["energy"])
+            mixed[name]["speedup_vs_fp64"] = mixed["fp64"]["sweep_ms"] / mixed[name]["sweep_ms"]
 
     if rank != 0:
         return
@@ -714,15 +742,28 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     if mixed is not None:
         line["mixed_vs_fp64_sweep"] = mixed
+    # the reference arm's sample on the GPU: FP64 products at the same window of the same
+    # random MPS (like-for-like with the oracle's milliseconds per product)
+    ms_p, fl_p = gpu_middle_window_product(b2, torch, ctx)
+    line["middle_window_product"] = {"ms": ms_p, "library_flops": fl_p,
+                                     "tflops": fl_p / (ms_p * 1e-3) / 1e12,
+                                     "input": "window (15, 16) of the workload's random MPS"}
+    if not args.no_window:
+        b2.b2_profile(ctx, True)
+        line["abinitio_n36_window"] = {
+            "M1000": window_leg(b2, torch, ctx, 1000, True, 3, peaks),
+            "M2000": window_leg(b2, torch, ctx, 2000, False, 3, peaks)}
+        b2.b2_profile(ctx, False)
     if not args.no_cpu_baseline and world == 1:
         budget = args.cpu_budget
-        sec, nprod, setup, bonds_c, sites_c, c, h_, eri_ = oracle_sample(budget)
-        fl = middle_window_flops(b2, ctx, h, eri, bonds_c, sites_c, c)
+        sec, nprod, setup, fl = oracle_sample(budget)
+        c = WORKLOAD["L"] // 2 - 1
         line["cpu_baseline"] = {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
                                 "kind": "oracle",
                                 "sample": "%d oracle H_eff.psi products at the middle window "
-                                          "(sites %d, %d) of the same workload; setup %.1f s"
-                                          % (nprod, c, c + 1, setup)}
+                                          "(sites %d, %d) of the workload's random MPS (setup "
+                                          "%.1f s, %.1f ms per product; flops counted by the "
+                                          "oracle)" % (nprod, c, c + 1, setup, sec * 1e3)}
     print(json.dumps(line), flush=True)
     b2.b2_free_env(env_h)
     b2.b2_free_mps(mps_h)

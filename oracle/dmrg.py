@@ -112,6 +112,8 @@ class Heff:
 
     def __init__(self, mpo, i, L, R, lab_l):
         self.terms = two_site_operators(mpo, i)
+        self.dq_l = mpo.dq[i]
+        self.dq_r = mpo.dq[i + 2]
         self.L, self.R = L, R
         self.par_l = parity_of(lab_l)
         self.pa = mpo.parity[i]
@@ -129,6 +131,40 @@ class Heff:
             Os = np.array([o for _, o in lst])                        # (nb, 16, 16)
             RsT = np.array([self.R[b].T for b, _ in lst])             # (nb, mr, mr')
             self.groups.append((La, Os, RsT))
+
+    def algorithmic_flops(self, lab_l, lab_r):
+        """Floating-point operations of the block-sparse form of this product: for every
+        operator pair (a, b), every nonzero local element O_ab[(s1' s2'), (s1 s2)] and every
+        pair of sectors (l, r) of psi that it connects to an existing output block (l', r'),
+        2 m_l' m_l m_r (L_a psi) + 2 m_l' m_r m_r' (times R_b^T).  Counts the work of the
+        product itself (used to express the oracle's speed in the unit of the benchmark)."""
+        def sectors(lab):
+            out = {}
+            for q in map(tuple, lab):
+                out[q] = out.get(q, 0) + 1
+            return out
+        ml, mr = sectors(lab_l), sectors(lab_r)
+        q = [tuple(x) for x in SITE_Q]
+        flops = 0.0
+        for (a, b), o in self.terms.items():
+            dqa = self.dq_l[a]
+            dqb = self.dq_r[b]
+            for u, v in zip(*np.nonzero(o)):
+                s1p, s2p, s1, s2 = u // 4, u % 4, v // 4, v % 4
+                for ql, m_l in ml.items():
+                    qr = (ql[0] + q[s1][0] + q[s2][0], ql[1] + q[s1][1] + q[s2][1])
+                    m_r = mr.get(qr)
+                    if m_r is None:
+                        continue
+                    qlp = (ql[0] + dqa[0], ql[1] + dqa[1])
+                    qrp = (qr[0] + dqb[0], qr[1] + dqb[1])
+                    m_lp, m_rp = ml.get(qlp), mr.get(qrp)
+                    if m_lp is None or m_rp is None:
+                        continue
+                    if (qlp[0] + q[s1p][0] + q[s2p][0], qlp[1] + q[s1p][1] + q[s2p][1]) != qrp:
+                        continue
+                    flops += 2.0 * m_lp * m_l * m_r + 2.0 * m_lp * m_r * m_rp
+        return flops
 
     def apply(self, psi):
         ml, mr = psi.shape[0], psi.shape[3]

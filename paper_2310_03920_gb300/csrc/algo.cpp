@@ -172,6 +172,7 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
   double host_sc[2];
   double brk = 0;
   bool stop_after_ritz = false;
+  std::vector<double> hist;   // residuals of the iterations so far
   for (;;) {
     cudaEvent_t r0 = nullptr, r1 = nullptr;
     if (c->prof) {
@@ -212,6 +213,11 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
     if (mv_prec != B2_FP64)
       B2_REQUIRE(c->take_status() == 0, B2_ETIMEOUT, "tensor-core wait ran out");
     if (stop_after_ritz || res.resid2 <= tol || nmv >= max_iter) break;
+    // split-precision products resolve the residual only down to their own error: once it
+    // has stopped falling (less than a factor 2 over four products), hand back to the FP64
+    // refinement instead of spending products on rounding noise
+    hist.push_back(res.resid2);
+    if (mv_prec != B2_FP64 && hist.size() > 4 && hist.back() > 0.5 * hist[hist.size() - 5]) break;
     if (k >= kmax) {   // restart from the Ritz vector
       B2_CUDA(cudaMemcpyAsync(Vp, u.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
       B2_CUDA(cudaMemcpyAsync(Wp, hu.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));

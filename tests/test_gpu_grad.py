@@ -203,7 +203,7 @@ def test_grad_n24_M500_against_oracle_transfer_matrices(ctx):
     assert np.abs(g1.ravel() - g_ref).max() <= 1e-11
     G_gpu = np.array([2.0 * g2[q4] for q4 in quads])
     assert np.abs(G_gpu - G_ref).max() <= 1e-11
-    # the comparison is not vacuous: many of the sampled elements are far from zero
-    assert np.sum(np.abs(G_ref) > 1e-3) > 40
+    # the comparison is not vacuous: many sampled elements are far above the tolerance
+    assert np.sum(np.abs(G_ref) > 1e-4) > 40 and np.sum(np.abs(g_ref) > 1e-2) > 24
     b2.b2_free_mps(s)
     b2.b2_free_mpo(m)
