@@ -754,8 +754,9 @@ void build_tc(Ctx* c, WindowProgram& wp) {
       tt.offA = env_operand(gt.bufP, gt.offP, o.M, gt.K1, gt.ldP);
       tt.offB1 = ip->second;
       tt.offB2 = env_operand(gt.bufQ, gt.offQ, o.N, gt.K2, gt.ldQ);
-      tt.K1 = gt.K1;
-      tt.K2 = gt.K2;
+      B2_REQUIRE(gt.K1 < 65536 && gt.K2 < 65536, B2_EUNSUPPORTED, "sector dimension above 65535");
+      tt.K1 = uint16_t(gt.K1);
+      tt.K2 = uint16_t(gt.K2);
       tt.alpha = static_cast<float>(gt.alpha);
       tp.terms.push_back(tt);
       cst += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
@@ -948,10 +949,20 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
 
 void heff_diag(b2_env_s* env, int site, double* diag) {
   WindowProgram& wp = window_program(env, site);
-  b2k::launch_diag(int(wp.diag_outs.size()), wp.d_diag_outs.as<b2k::DiagOut>(),
-                   wp.d_diag_terms.as<b2k::DiagTerm>(), env->L[site].data.as<double>(),
-                   env->R[site + 2].data.as<double>(), diag, env->ctx->stream);
-  B2_CUDA(cudaGetLastError());
+  Ctx* c = env->ctx;
+  // the diagonal depends only on the window's environments: computed once per window
+  // program, copied out on later calls (the Davidson solver asks for it every solve)
+  if (!wp.diag_done) {
+    wp.diag.reset(c, sizeof(double) * size_t(std::max<int64_t>(wp.psi.size, 1)));
+    b2k::launch_diag(int(wp.diag_outs.size()), wp.d_diag_outs.as<b2k::DiagOut>(),
+                     wp.d_diag_terms.as<b2k::DiagTerm>(), env->L[site].data.as<double>(),
+                     env->R[site + 2].data.as<double>(), wp.diag.as<double>(), c->stream);
+    B2_CUDA(cudaGetLastError());
+    wp.diag_done = true;
+  }
+  if (wp.psi.size > 0)
+    B2_CUDA(cudaMemcpyAsync(diag, wp.diag.ptr, sizeof(double) * size_t(wp.psi.size),
+                            cudaMemcpyDeviceToDevice, c->stream));
 }
 
 }  // namespace b2

@@ -91,6 +91,8 @@ struct WindowProgram {
   std::vector<b2k::DiagOut> diag_outs;
   std::vector<b2k::DiagTerm> diag_terms;
   DevBuf d_diag_outs, d_diag_terms;
+  DevBuf diag;              // the diagonal, computed on first use (environments are fixed)
+  bool diag_done = false;
   bool comb_done = false;
   TcProgram tc;
 };

@@ -132,11 +132,12 @@ struct TcOut {
 // out += alpha * L [M x K1] psi [K1 x K2] R^T [K2 x N]; offA / offB2: element offsets of the
 // split L and R operands (rows M / N, K = K1 / K2) in the environment planes, offB1: of the
 // split psi^T block (rows K2, K = K1) in the psi planes.
-struct TcTerm {
+struct TcTerm {   // 32 bytes: batches of them are copied into shared memory
   int64_t offA, offB1, offB2;
-  int K1, K2;
+  uint16_t K1, K2;
   float alpha;
 };
+static_assert(sizeof(TcTerm) == 32, "TcTerm is moved in 16-byte units");
 struct TcTile {
   int out, r0, c0;
 };

@@ -21,11 +21,13 @@
 // each product formed as hi*hi + hi*lo + lo*hi; acc is added to the FP64 output block at
 // the end (overwritten or accumulated).
 //
-// Roles (6 warps): warp 0 streams operand chunks through a 3-stage shared-memory ring with
-// cp.async.bulk (completion on the stage's mbarrier); one thread of warp 1 issues the MMAs;
-// warps 2-5 (one per TMEM lane quarter) convert T into T' and write the result.  The MMA
-// thread computes T of the next chain unit while the converter works on the current one
-// (two T buffers in TMEM, two T' buffers in shared memory).  Every wait is bounded: a wait
+// Roles (10 warps): warp 0 streams operand chunks through a byte ring of shared memory with
+// cp.async.bulk (completion on the item's mbarrier); one thread of warp 1 issues the MMAs;
+// warps 2-9 (two per TMEM lane quarter) convert T into T' and add the accumulators to the
+// output.  The MMA thread computes T of the next chain unit while the converter works on
+// the current one (two T buffers in TMEM, two T' buffers in shared memory); the sum over a
+// tile's units runs in groups of kGroup units in two TMEM accumulators, each group added to
+// the FP64 output by the converter warps while the other accumulator fills.  Every wait is bounded: a wait
 // that runs out sets the CTA's abort flag and the status word; the other roles then stop,
 // the producer waits (with the full limit) for its copies in flight, the MMA thread for its
 // MMAs, TMEM is freed and the CTA returns.  For tests of that path, stuck_polls > 0 makes
@@ -41,12 +43,16 @@ namespace b2k {
 
 namespace {
 
-constexpr int kStages = 3;
-constexpr int kPBytes = 128 * 128;                   // <= 128 rows x one 128-byte K chunk
-constexpr int kQBytes = 64 * 128;                    // <= 64 rows (one T chunk of psi^T)
-constexpr int kStageBytes = 2 * kPBytes + 2 * kQBytes;
-constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo
-constexpr int kDynSmem = kStages * kStageBytes + 2 * kTpBytes + 1024;
+// Operand chunks stream through a byte ring of shared memory: each item (the chunks one
+// MMA group reads: L and psi^T for MMA1, R for MMA2, hi and lo planes) takes exactly its
+// size, so many small blocks are in flight at once; at most kSlots items are outstanding.
+constexpr int kSlots = 16;
+constexpr int kRingBytes = 152 * 1024;
+constexpr int kPBytes = 128 * 128;                   // 128 rows x one 128-byte K chunk
+constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo (follows the ring: an A
+                                                     // operand read past its item's rows stays
+                                                     // inside shared memory)
+constexpr int kDynSmem = kRingBytes + 2 * kTpBytes + 1024;
 constexpr int kThreads = 320;                        // producer, MMA, 8 converter warps
 constexpr int kConv = 256;                           // converter threads
 // TMEM columns: T0 [0,64), T1 [64,128), acc0 [128,256), acc1 [256,384)
@@ -193,11 +199,6 @@ __device__ __forceinline__ void split_tf32(float f, uint32_t& hi, uint32_t& lo) 
 
 __host__ __device__ __forceinline__ int pad16(int x) { return (x + 15) & ~15; }
 
-// chain units of one tile: (term t, 128-byte chunk c of K2), terms in order
-struct Unit {
-  int t, c;
-};
-
 }  // namespace
 
 // byte offset of chunk c of a pre-tiled block of rp rows (chunks before c are full)
@@ -258,20 +259,44 @@ __global__ void __launch_bounds__(256) k_split(const SplitTask* __restrict__ tas
 }
 
 // ------------------------------------------------------------------ the contraction
+namespace {
+constexpr int kTermBatch = 64;   // terms copied into shared memory per bulk copy
+constexpr int kUnitRing = 32;    // unit descriptors in flight between producer and converter
+// what the MMA thread needs of one ring item (written by the producer before the item's
+// copies are armed, so the full barrier orders it)
+struct ItemMeta {
+  uint32_t pos;      // ring offset of the item
+  uint32_t a, b;     // bytes of one plane of the first / second operand
+  uint16_t kg, n1;   // k-groups of the chunk, T columns of the unit
+  uint8_t kind;      // 0: MMA1 chunk, 1: MMA2
+  uint8_t first, last;   // MMA1: first / last K1 chunk of the unit; MMA2: last unit of the tile
+};
+// what the converter needs of one chain unit
+struct UnitMeta {
+  float alpha;
+  int n1;
+  int last;          // last unit of the tile
+};
+}  // namespace
+
 __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile, int* status,
                                              uint32_t stuck_polls, bool tf32) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
   __shared__ __align__(8) uint64_t tfull[2], tempty[2], tpready[2], tpempty[2], drainb;
   __shared__ __align__(8) uint64_t accfull[2], accempty[2];
+  __shared__ __align__(8) uint64_t ufull[kUnitRing], uempty[kUnitRing], tbfull[2];
   __shared__ __align__(8) uint64_t neverb;   // nothing arrives on it (failure-path tests)
+  __shared__ __align__(16) TcTerm tbatch[2][kTermBatch];
+  __shared__ ItemMeta imeta[kSlots];
+  __shared__ UnitMeta umeta[kUnitRing];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stage_mem = base;
-  unsigned char* tp_mem = base + kStages * kStageBytes;
+  unsigned char* ring = base;
+  unsigned char* tp_mem = base + kRingBytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int es = tf32 ? 4 : 2;
@@ -284,7 +309,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
   const uint32_t limit = kDefaultWait;
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kSlots; ++s) {
       bar_init(&full[s], 1);
       bar_init(&empty[s], 1);
     }
@@ -295,6 +320,11 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       bar_init(&tpempty[b], 1);
       bar_init(&accfull[b], 1);
       bar_init(&accempty[b], kConv);
+      bar_init(&tbfull[b], 1);
+    }
+    for (int k = 0; k < kUnitRing; ++k) {
+      bar_init(&ufull[k], 1);
+      bar_init(&uempty[k], kConv);
     }
     bar_init(&drainb, 1);
     bar_init(&neverb, 1);
@@ -317,192 +347,238 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     atomicExch(status, 1);
   };
   auto nchunks = [&](int k) { return (pad16(k) * es + 127) / 128; };
-  auto next = [&](Unit& u) {
-    if (++u.c >= nchunks(G.terms[u.t].K2)) {
-      ++u.t;
-      u.c = 0;
-    }
-  };
-  const Unit first{o.t0, 0};
+  const int n_terms = o.t1 - o.t0;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // The only role that reads the term list: batches of kTermBatch terms are copied into
+    // shared memory two ahead; every item carries what the MMA thread needs (imeta), every
+    // unit what the converter needs (umeta).
     if (lane == 0) {
-      uint32_t item = 0;
+      uint32_t item = 0, oldest = 0;   // items issued / first item not known consumed
+      uint32_t head = 0, used = 0;     // next ring offset, bytes held by in-flight items
+      uint32_t foot[kSlots];           // ring bytes of the in-flight item of each slot
       bool ok = true;
-      auto acquire = [&](int& s) -> bool {
-        s = int(item % kStages);
-        if (item >= kStages && !bar_wait(&empty[s], ((item / kStages) & 1) ^ 1, limit, &abort_flag)) {
+      const int n_batches = (n_terms + kTermBatch - 1) / kTermBatch;
+      auto issue_batch = [&](int bt) {
+        const int cnt = min(kTermBatch, n_terms - bt * kTermBatch);
+        const uint32_t bytes = uint32_t(cnt) * uint32_t(sizeof(TcTerm));
+        bar_expect_tx(&tbfull[bt & 1], bytes);
+        bulk_g2s(smem_u32(&tbatch[bt & 1][0]), G.terms + o.t0 + bt * kTermBatch, bytes,
+                 &tbfull[bt & 1]);
+      };
+      int cur_batch = -1;
+      // term t (relative to o.t0), waiting for its batch and arming the one after it (the
+      // slot it goes to held the batch before this one, which this thread has finished)
+      auto term = [&](int t, TcTerm& tm) -> bool {
+        const int bt = t / kTermBatch;
+        if (bt != cur_batch) {
+          if (!bar_wait(&tbfull[bt & 1], (bt >> 1) & 1, limit, &abort_flag)) {
+            if (!abort_flag) fail();
+            return false;
+          }
+          cur_batch = bt;
+          if (bt + 1 < n_batches && bt >= 1) {
+            // this thread's reads of the slot (batch bt - 1) come before the copy's writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_batch(bt + 1);
+          }
+        }
+        tm = tbatch[bt & 1][t % kTermBatch];
+        return true;
+      };
+      // the oldest in-flight item has been consumed: its bytes are free again
+      auto retire = [&]() -> bool {
+        const int s = int(oldest % kSlots);
+        if (!bar_wait(&empty[s], (oldest / kSlots) & 1, limit, &abort_flag)) {
           if (!abort_flag) fail();
           return false;
         }
+        used -= foot[s];
+        ++oldest;
         return true;
       };
-      auto produce_x = [&](const Unit& u) -> bool {
-        const TcTerm tm = G.terms[u.t];
-        const int kp1 = pad16(tm.K1), rp1 = pad16(tm.K2);
-        const int rowsB1 = min(wk, rp1 - u.c * wk);
-        for (int c = 0; c < nchunks(tm.K1); ++c) {
-          int s;
-          if (!acquire(s)) return false;
-          const int kg = tc_chunk_kg(kp1, es, c);
-          const uint32_t bA = uint32_t(rowsA) * kg * 16, bB = uint32_t(rowsB1) * kg * 16;
-          const int64_t oA = tm.offA * es + tc_chunk_off(pad16(o.M), c) + int64_t(r0 >> 3) * kg * 128;
-          const int64_t oB = tm.offB1 * es + tc_chunk_off(rp1, c) + int64_t((u.c * wk) >> 3) * kg * 128;
-          unsigned char* st = stage_mem + s * kStageBytes;
-          bar_expect_tx(&full[s], 2 * (bA + bB));
-          bulk_g2s(smem_u32(st), G.env_hi + oA, bA, &full[s]);
-          bulk_g2s(smem_u32(st + kPBytes), G.env_lo + oA, bA, &full[s]);
-          bulk_g2s(smem_u32(st + 2 * kPBytes), G.psi_hi + oB, bB, &full[s]);
-          bulk_g2s(smem_u32(st + 2 * kPBytes + kQBytes), G.psi_lo + oB, bB, &full[s]);
-          ++item;
+      // a slot and sz contiguous ring bytes (wrapping to offset 0 when the end is too close;
+      // the skipped bytes count with the item until it is consumed)
+      auto acquire = [&](uint32_t sz, int& s, uint32_t& pos) -> bool {
+        while (item - oldest >= uint32_t(kSlots))
+          if (!retire()) return false;
+        for (;;) {
+          const bool fits = head + sz <= uint32_t(kRingBytes);
+          const uint32_t fp = fits ? sz : (uint32_t(kRingBytes) - head) + sz;
+          if (fp <= uint32_t(kRingBytes) - used) {
+            pos = fits ? head : 0;
+            s = int(item % kSlots);
+            foot[s] = fp;
+            used += fp;
+            head = pos + sz;
+            return true;
+          }
+          if (!retire()) return false;
         }
-        return true;
       };
-      auto produce_y = [&](const Unit& u) -> bool {
-        const TcTerm tm = G.terms[u.t];
-        const int kp2 = pad16(tm.K2);
-        int s;
-        if (!acquire(s)) return false;
-        const int kg = tc_chunk_kg(kp2, es, u.c);
+      // Y item of a unit (R chunk), from the values kept when its X items were produced
+      struct PendY {
+        int64_t offB2;
+        int K2, c;
+        bool last;
+      };
+      auto produce_y = [&](const PendY& py) -> bool {
+        const int kg = tc_chunk_kg(pad16(py.K2), es, py.c);
         const uint32_t b = uint32_t(rowsB2) * kg * 16;
-        const int64_t oR = tm.offB2 * es + tc_chunk_off(pad16(o.N), u.c) + int64_t(c0 >> 3) * kg * 128;
-        unsigned char* st = stage_mem + s * kStageBytes;
+        int s;
+        uint32_t pos;
+        if (!acquire(2 * b, s, pos)) return false;
+        imeta[s] = ItemMeta{pos, b, 0, uint16_t(kg), uint16_t(pad16(min(wk, py.K2 - py.c * wk))),
+                            1, 0, uint8_t(py.last ? 1 : 0)};
+        const int64_t oR = py.offB2 * es + tc_chunk_off(pad16(o.N), py.c) + int64_t(c0 >> 3) * kg * 128;
+        const uint32_t st = smem_u32(ring + pos);
         bar_expect_tx(&full[s], 2 * b);
-        bulk_g2s(smem_u32(st), G.env_hi + oR, b, &full[s]);
-        bulk_g2s(smem_u32(st + kPBytes), G.env_lo + oR, b, &full[s]);
+        bulk_g2s(st, G.env_hi + oR, b, &full[s]);
+        bulk_g2s(st + b, G.env_lo + oR, b, &full[s]);
         ++item;
         return true;
       };
-      Unit ux = first, uy = first;
-      if (ux.t < o.t1) {
-        ok = produce_x(ux);
-        next(ux);
-      }
-      while (ok && uy.t < o.t1 && !abort_flag) {
-        if (ux.t < o.t1) {
-          ok = produce_x(ux);
-          next(ux);
+      issue_batch(0);
+      if (n_batches > 1) issue_batch(1);
+      uint32_t ui = 0;   // units produced
+      PendY pend{};
+      bool have_pend = false;
+      for (int t = 0; t < n_terms && ok && !abort_flag; ++t) {
+        TcTerm tm;
+        if (!(ok = term(t, tm))) break;
+        const int nch2 = nchunks(tm.K2), nch1 = nchunks(tm.K1);
+        const int kp1 = pad16(tm.K1), rp1 = pad16(tm.K2);
+        for (int c2 = 0; c2 < nch2 && ok; ++c2, ++ui) {
+          const bool last_unit = (t == n_terms - 1) && (c2 == nch2 - 1);
+          const int n1 = pad16(min(wk, int(tm.K2) - c2 * wk));
+          // the converter's descriptor of this unit
+          const int k = int(ui % kUnitRing);
+          if (ui >= uint32_t(kUnitRing) &&
+              !bar_wait(&uempty[k], ((ui / kUnitRing) & 1) ^ 1, limit, &abort_flag)) {
+            if (!abort_flag) fail();
+            ok = false;
+            break;
+          }
+          umeta[k] = UnitMeta{tm.alpha, n1, last_unit ? 1 : 0};
+          bar_arrive(&ufull[k]);
+          // X items: the K1 chunks of L and psi^T
+          const int rowsB1 = min(wk, rp1 - c2 * wk);
+          for (int c = 0; c < nch1; ++c) {
+            const int kg = tc_chunk_kg(kp1, es, c);
+            const uint32_t bA = uint32_t(rowsA) * kg * 16, bB = uint32_t(rowsB1) * kg * 16;
+            int s;
+            uint32_t pos;
+            if (!(ok = acquire(2 * (bA + bB), s, pos))) break;
+            imeta[s] = ItemMeta{pos, bA, bB, uint16_t(kg), uint16_t(n1), 0, uint8_t(c == 0),
+                                uint8_t(c == nch1 - 1)};
+            const int64_t oA = tm.offA * es + tc_chunk_off(pad16(o.M), c) + int64_t(r0 >> 3) * kg * 128;
+            const int64_t oB = tm.offB1 * es + tc_chunk_off(rp1, c) + int64_t((c2 * wk) >> 3) * kg * 128;
+            const uint32_t st = smem_u32(ring + pos);
+            bar_expect_tx(&full[s], 2 * (bA + bB));
+            bulk_g2s(st, G.env_hi + oA, bA, &full[s]);
+            bulk_g2s(st + bA, G.env_lo + oA, bA, &full[s]);
+            bulk_g2s(st + 2 * bA, G.psi_hi + oB, bB, &full[s]);
+            bulk_g2s(st + 2 * bA + bB, G.psi_lo + oB, bB, &full[s]);
+            ++item;
+          }
           if (!ok) break;
+          // then the Y item of the previous unit (the MMA thread computes T of this unit
+          // before it multiplies the previous one by R)
+          if (have_pend && !(ok = produce_y(pend))) break;
+          pend = PendY{tm.offB2, int(tm.K2), c2, last_unit};
+          have_pend = true;
         }
-        ok = produce_y(uy);
-        next(uy);
       }
-      // drain: the copies of the last item of every stage have landed
-      for (int s = 0; s < kStages; ++s) {
-        if (uint32_t(s) >= item) continue;
-        const uint32_t last = item - 1 - ((item - 1 - s) % kStages);
-        if (!bar_drain(&full[s], (last / kStages) & 1)) fail();
+      if (ok && have_pend && !abort_flag) ok = produce_y(pend);
+      // drain: every copy issued has landed before the CTA can exit (items already
+      // consumed complete at once); the term batches too
+      for (uint32_t i = oldest; i < item; ++i)
+        if (!bar_drain(&full[i % kSlots], (i / kSlots) & 1)) fail();
+      if (cur_batch + 1 < n_batches) {   // batches armed but never waited for
+        for (int bt = cur_batch + 1; bt < min(n_batches, max(cur_batch, 0) + 2); ++bt)
+          if (!bar_drain(&tbfull[bt & 1], (bt >> 1) & 1)) fail();
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // Items in the producer's order: the MMA1 chunks of unit u+1, then the MMA2 of unit u.
     if (lane == 0) {
-      uint32_t item = 0;
+      uint32_t item = 0, ix = 0, iy = 0;
       bool ok = true;
-      const uint32_t t_base = tmem;
-      const uint32_t id2 = idesc(n2, tf32);
-      auto take = [&](int& s) -> bool {
-        s = int(item % kStages);
-        if (!bar_wait(&full[s], (item / kStages) & 1, limit, &abort_flag)) {
-          if (!abort_flag) fail();
-          return false;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        return true;
-      };
-      auto mma1 = [&](const Unit& u, uint32_t idx) -> bool {
-        const int b = idx & 1;
-        if (idx >= 2 && !bar_wait(&tempty[b], ((idx >> 1) & 1) ^ 1, limit, &abort_flag)) {
-          if (!abort_flag) fail();
-          return false;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const TcTerm tm = G.terms[u.t];
-        const int kp1 = pad16(tm.K1);
-        const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
-        const uint32_t id1 = idesc(n1, tf32);
-        const uint32_t tT = t_base + uint32_t(b * 64);
-        for (int c = 0; c < nchunks(tm.K1); ++c) {
-          int s;
-          if (!take(s)) return false;
-          const int kg = tc_chunk_kg(kp1, es, c);
-          const uint32_t sbo = uint32_t(kg) * 128;
-          const uint32_t st = smem_u32(stage_mem + s * kStageBytes);
-          const uint32_t aH = st, aL = st + kPBytes, bH = st + 2 * kPBytes, bL = st + 2 * kPBytes + kQBytes;
-          for (int ks = 0; ks < kg / 2; ++ks) {
-            const uint32_t off = uint32_t(ks) * 256;
-            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bH + off, sbo), id1, (c > 0 || ks > 0) ? 1u : 0u);
-            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bL + off, sbo), id1, 1u);
-            mma(tf32, tT, sdesc(aL + off, sbo), sdesc(bH + off, sbo), id1, 1u);
-          }
-          commit(&empty[s]);
-          ++item;
-        }
-        commit(&tfull[b]);
-        return true;
-      };
-      // MMA2 of unit idx into accumulator (idx / kGroup) & 1; the first unit of a group
-      // overwrites it (after the converter has added the group two back to the output),
-      // the last one signals it full
-      auto mma2 = [&](const Unit& u, uint32_t idx, bool last) -> bool {
-        const int b = idx & 1;
-        const uint32_t g = idx / kGroup;
-        const int ab = int(g & 1);
-        const bool gstart = (idx % kGroup) == 0;
-        if (gstart && g >= 2 && !bar_wait(&accempty[ab], ((g >> 1) & 1) ^ 1, limit, &abort_flag)) {
-          if (!abort_flag) fail();
-          return false;
-        }
-        if (!bar_wait(&tpready[b], (idx >> 1) & 1, limit, &abort_flag)) {
-          if (!abort_flag) fail();
-          return false;
-        }
-        int s;
-        if (!take(s)) return false;
-        const TcTerm tm = G.terms[u.t];
-        const int kg = tc_chunk_kg(pad16(tm.K2), es, u.c);
-        const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
-        const int ksteps = n1 * es / 32;
-        const uint32_t st = smem_u32(stage_mem + s * kStageBytes);
-        const uint32_t tpH = smem_u32(tp_mem + b * kTpBytes), tpL = tpH + kPBytes;
-        const uint32_t sbo = uint32_t(kg) * 128;
-        const uint32_t acc_tm = tmem + 128u + uint32_t(ab) * 128u;
-        for (int ks = 0; ks < ksteps; ++ks) {
-          const uint32_t off = uint32_t(ks) * 256;
-          mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + off, sbo), id2,
-              (!gstart || ks > 0) ? 1u : 0u);
-          mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + kPBytes + off, sbo), id2, 1u);
-          mma(tf32, acc_tm, sdesc(tpL + off, 1024), sdesc(st + off, sbo), id2, 1u);
-        }
-        commit(&empty[s]);
-        commit(&tpempty[b]);
-        if (last || idx % kGroup == kGroup - 1) commit(&accfull[ab]);
-        ++item;
-        return true;
-      };
-      Unit ux = first, uy = first;
-      uint32_t ix = 0, iy = 0;
       if (stuck_polls) {
         // failure-path test: a bounded wait on a barrier nothing arrives on runs out
         if (!bar_wait(&neverb, 0, stuck_polls, &abort_flag) && !abort_flag) fail();
         ok = false;
       }
-      if (ok && ux.t < o.t1) {
-        ok = mma1(ux, ix++);
-        next(ux);
-      }
-      while (ok && uy.t < o.t1) {
-        if (ux.t < o.t1) {
-          ok = mma1(ux, ix++);
-          next(ux);
-          if (!ok) break;
+      bool done = false;
+      while (ok && !done) {
+        const int s = int(item % kSlots);
+        if (!bar_wait(&full[s], (item / kSlots) & 1, limit, &abort_flag)) {
+          if (!abort_flag) fail();
+          break;
         }
-        Unit un = uy;
-        next(un);
-        ok = mma2(uy, iy++, un.t >= o.t1);
-        uy = un;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const ItemMeta im = imeta[s];
+        const uint32_t st = smem_u32(ring + im.pos);
+        const uint32_t sbo = uint32_t(im.kg) * 128;
+        if (im.kind == 0) {
+          // MMA1 chunk of unit ix: T[ix & 1] (+)= L psi^T chunk
+          const int b = ix & 1;
+          if (im.first && ix >= 2 && !bar_wait(&tempty[b], ((ix >> 1) & 1) ^ 1, limit, &abort_flag)) {
+            if (!abort_flag) fail();
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t id1 = idesc(im.n1, tf32);
+          const uint32_t tT = tmem + uint32_t(b * 64);
+          const uint32_t aH = st, aL = st + im.a, bH = st + 2 * im.a, bL = st + 2 * im.a + im.b;
+          for (int ks = 0; ks < im.kg / 2; ++ks) {
+            const uint32_t off = uint32_t(ks) * 256;
+            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bH + off, sbo), id1, (!im.first || ks > 0) ? 1u : 0u);
+            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bL + off, sbo), id1, 1u);
+            mma(tf32, tT, sdesc(aL + off, sbo), sdesc(bH + off, sbo), id1, 1u);
+          }
+          commit(&empty[s]);
+          if (im.last) {
+            commit(&tfull[b]);
+            ++ix;
+          }
+        } else {
+          // MMA2 of unit iy into accumulator (iy / kGroup) & 1: the first unit of a group
+          // overwrites it (after the converter has added the group two back to the output)
+          const int b = iy & 1;
+          const uint32_t g = iy / kGroup;
+          const int ab = int(g & 1);
+          const bool gstart = (iy % kGroup) == 0;
+          if (gstart && g >= 2 && !bar_wait(&accempty[ab], ((g >> 1) & 1) ^ 1, limit, &abort_flag)) {
+            if (!abort_flag) fail();
+            break;
+          }
+          if (!bar_wait(&tpready[b], (iy >> 1) & 1, limit, &abort_flag)) {
+            if (!abort_flag) fail();
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t tpH = smem_u32(tp_mem + b * kTpBytes), tpL = tpH + kPBytes;
+          const uint32_t acc_tm = tmem + 128u + uint32_t(ab) * 128u;
+          const uint32_t id2 = idesc(n2, tf32);
+          const int ksteps = im.n1 * es / 32;
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t off = uint32_t(ks) * 256;
+            mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + off, sbo), id2,
+                (!gstart || ks > 0) ? 1u : 0u);
+            mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + im.a + off, sbo), id2, 1u);
+            mma(tf32, acc_tm, sdesc(tpL + off, 1024), sdesc(st + off, sbo), id2, 1u);
+          }
+          commit(&empty[s]);
+          commit(&tpempty[b]);
+          if (im.last || iy % kGroup == kGroup - 1) commit(&accfull[ab]);
+          done = im.last;
+          ++iy;
+        }
+        ++item;
       }
       // every MMA issued has finished before TMEM is freed
       commit(&drainb);
@@ -547,11 +623,13 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       }
       return true;
     };
-    Unit u = first;
     uint32_t idx = 0;
-    while (u.t < o.t1) {
+    bool last = false;
+    while (!last) {
       const int b = idx & 1;
-      bool w = bar_wait(&tfull[b], (idx >> 1) & 1, limit, &abort_flag);
+      const int k = int(idx % kUnitRing);
+      bool w = bar_wait(&ufull[k], (idx / kUnitRing) & 1, limit, &abort_flag);
+      if (w) w = bar_wait(&tfull[b], (idx >> 1) & 1, limit, &abort_flag);
       if (w && idx >= 2) w = bar_wait(&tpempty[b], ((idx >> 1) & 1) ^ 1, limit, &abort_flag);
       if (!__all_sync(0xffffffffu, w)) {
         if (!abort_flag) fail();
@@ -559,9 +637,11 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const TcTerm tm = G.terms[u.t];
-      const float alpha = tm.alpha;
-      const int n1 = pad16(min(wk, tm.K2 - u.c * wk));
+      const UnitMeta um = umeta[k];
+      bar_arrive(&uempty[k]);
+      last = um.last != 0;
+      const float alpha = um.alpha;
+      const int n1 = um.n1;
       const int cb = half * hw;
       unsigned char* tpH = tp_mem + b * kTpBytes;
       unsigned char* tpL = tpH + kPBytes;
@@ -609,7 +689,6 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         ok = false;
         break;
       }
-      next(u);
       ++idx;
     }
     if (ok && idx > 0 && !flush((idx - 1) / kGroup)) ok = false;
