@@ -48,6 +48,7 @@ struct DavState {
   int k = 1, nmv = 0;
   int dims_h = 0;
   bool active = true;
+  std::vector<double> hist;   // residuals so far (stagnation test of split products)
   DavidsonResult res;
 };
 
@@ -87,6 +88,7 @@ void davidson_batched_core(Ctx* c, std::vector<DavState>& st, const b2_dav_opts&
     s.k = 1;
     s.nmv = 0;
     s.active = true;
+    s.hist.clear();
     s.res = DavidsonResult{};
     heff_diag(s.env, s.site, s.diag.as<double>());
     b2k::launch_multidot(1, s.psi, s.n, s.psi, s.n, s.part, s.scal + 2, 1, c->stream);
@@ -163,6 +165,12 @@ void davidson_batched_core(Ctx* c, std::vector<DavState>& st, const b2_dav_opts&
       B2_REQUIRE(std::isfinite(s.res.resid2) && std::isfinite(s.res.energy), B2_ENOCONV,
                  "Davidson produced a non-finite value");
       if (s.res.resid2 <= s.tol || s.nmv >= s.max_iter) {
+        s.active = false;
+        continue;
+      }
+      // the same stagnation stop as the single-problem solver (split-precision products)
+      s.hist.push_back(s.res.resid2);
+      if (mv_prec != B2_FP64 && s.hist.size() > 4 && s.hist.back() > 0.5 * s.hist[s.hist.size() - 5]) {
         s.active = false;
         continue;
       }

@@ -665,23 +665,80 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
   for (int v = 0; v < 16; ++v)
     for (const auto& e : pat[v * 16 + v])
       if (mpo->dq[i][e.a] == QN{0, 0} && mpo->dq[i + 2][e.b] == QN{0, 0}) dedges[v].push_back(e);
-  for (const auto& pb : wp.psi.blocks) {
-    b2k::DiagOut d;
-    d.off = pb.off;
-    d.ml = pb.ml;
-    d.mr = pb.mr;
-    d.t0 = int(wp.diag_terms.size());
-    for (const auto& e : dedges[pb.s1 * 4 + pb.s2]) {
-      int lb = L.blk[e.a][pb.jl], rb = R.blk[e.b][pb.jr];
-      if (lb < 0 || rb < 0) continue;
-      double sign = (mpo->parity[i][e.a] && par_n(bl.q[pb.jl].n)) ? -1.0 : 1.0;
-      wp.diag_terms.push_back({L.blocks[lb].off, R.blocks[rb].off, sign * e.v});
+  {
+    // channel rows of the diagonal buffers
+    std::vector<int> ka(Da, -1), kb(Db, -1);
+    int KA = 0, KB = 0;
+    for (int v = 0; v < 16; ++v)
+      for (const auto& e : dedges[v]) {
+        B2_REQUIRE(mpo->parity[i][e.a] == 0 && mpo->parity[i + 2][e.b] == 0, B2_EINVAL,
+                   "internal: odd channel on the diagonal");
+        if (ka[e.a] < 0) ka[e.a] = KA++;
+        if (kb[e.b] < 0) kb[e.b] = KB++;
+      }
+    const int64_t SL = bl.total, SR = br.total;
+    const int64_t offDR = int64_t(KA) * SL, offS = offDR + int64_t(KB) * SR;
+    wp.dg_size = offS + int64_t(16) * KA * SR;
+    // diagonals of the blocks (dst row = channel, columns = the bond's states)
+    for (int a = 0; a < Da; ++a) {
+      if (ka[a] < 0) continue;
+      for (int j = 0; j < bl.size(); ++j) {
+        const int b = L.blk[a][j];
+        if (b < 0) continue;
+        B2_REQUIRE(L.blocks[b].jb == j, B2_EINVAL, "internal: diagonal block");
+        wp.dg_copy.push_back({L.blocks[b].off, int64_t(ka[a]) * SL + bl.off[j], bl.m[j], 1,
+                              bl.m[j] + 1, 1, 0, 2, 5});
+      }
     }
-    d.t1 = int(wp.diag_terms.size());
-    wp.diag_outs.push_back(d);
+    for (int b = 0; b < Db; ++b) {
+      if (kb[b] < 0) continue;
+      for (int j = 0; j < br.size(); ++j) {
+        const int rb = R.blk[b][j];
+        if (rb < 0) continue;
+        B2_REQUIRE(R.blocks[rb].jb == j, B2_EINVAL, "internal: diagonal block");
+        wp.dg_copy.push_back({R.blocks[rb].off, offDR + int64_t(kb[b]) * SR + br.off[j], br.m[j], 1,
+                              br.m[j] + 1, 1, 0, 3, 5});
+      }
+    }
+    // S rows: per pattern v and left channel a, sum over its edges of c * dR_b
+    std::vector<int> order;
+    for (int v = 0; v < 16; ++v) {
+      auto& ed = dedges[v];
+      order.resize(ed.size());
+      for (size_t k = 0; k < ed.size(); ++k) order[k] = int(k);
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ed[x].a < ed[y].a; });
+      for (size_t k = 0; k < order.size();) {
+        const int a = ed[order[k]].a;
+        b2k::CombOut co;
+        co.off = offS + (int64_t(v) * KA + ka[a]) * SR;
+        co.n = SR;
+        co.buf = 5;
+        co.t0 = int(wp.dg_comb.terms.size());
+        for (; k < order.size() && ed[order[k]].a == a; ++k) {
+          const Edge& e = ed[order[k]];
+          wp.dg_comb.terms.push_back({offDR + int64_t(kb[e.b]) * SR, e.v, 5});
+        }
+        co.t1 = int(wp.dg_comb.terms.size());
+        wp.dg_comb.outs.push_back(co);
+      }
+    }
+    // one product per psi block: diag[l][r] = sum_k dL[k][l] S_v[k][r]
+    for (const auto& pb : wp.psi.blocks) {
+      const int v = pb.s1 * 4 + pb.s2;
+      const int o = wp.dg_gemm.add_out(1, pb.off, pb.ml, pb.mr, pb.mr, false);
+      if (dedges[v].empty() || KA == 0) continue;
+      GemmTerm t{};
+      t.offP = bl.off[pb.jl]; t.bufP = 5; t.ldP = int(SL);
+      t.offX = offS + int64_t(v) * KA * SR + br.off[pb.jr]; t.bufX = 5; t.ldX = int(SR);
+      t.K1 = KA;
+      t.flags = kTwoOp | kTransP;
+      t.alpha = 1.0;
+      wp.dg_gemm.add_term(o, t);
+    }
+    upload(c, wp.d_dg_copy, wp.dg_copy);
+    if (!wp.dg_comb.outs.empty()) wp.dg_comb.finalize(c);
+    wp.dg_gemm.finalize(c);
   }
-  upload(c, wp.d_diag_outs, wp.diag_outs);
-  upload(c, wp.d_diag_terms, wp.diag_terms);
   wp.comb_done = false;
 }
 
@@ -954,9 +1011,16 @@ void heff_diag(b2_env_s* env, int site, double* diag) {
   // program, copied out on later calls (the Davidson solver asks for it every solve)
   if (!wp.diag_done) {
     wp.diag.reset(c, sizeof(double) * size_t(std::max<int64_t>(wp.psi.size, 1)));
-    b2k::launch_diag(int(wp.diag_outs.size()), wp.d_diag_outs.as<b2k::DiagOut>(),
-                     wp.d_diag_terms.as<b2k::DiagTerm>(), env->L[site].data.as<double>(),
-                     env->R[site + 2].data.as<double>(), wp.diag.as<double>(), c->stream);
+    DevBuf work(c, sizeof(double) * size_t(std::max<int64_t>(wp.dg_size, 1)));
+    B2_CUDA(cudaMemsetAsync(work.ptr, 0, work.bytes, c->stream));
+    BufTable bt{};
+    bt.p[1] = wp.diag.as<double>();
+    bt.p[2] = env->L[site].data.as<double>();
+    bt.p[3] = env->R[site + 2].data.as<double>();
+    bt.p[5] = work.as<double>();
+    b2k::launch_copy(int(wp.dg_copy.size()), wp.d_dg_copy.as<b2k::CopyTask>(), bt, c->stream);
+    if (!wp.dg_comb.outs.empty()) wp.dg_comb.launch(c, bt);
+    wp.dg_gemm.launch(c, bt);
     B2_CUDA(cudaGetLastError());
     wp.diag_done = true;
   }

@@ -88,9 +88,17 @@ struct WindowProgram {
   GemmProgram heff;        // bufs: 0 psi, 1 out, 2 L env, 3 R env, 4 combination buffer
   CombProgram comb;
   DevBuf comb_buf;
-  std::vector<b2k::DiagOut> diag_outs;
-  std::vector<b2k::DiagTerm> diag_terms;
-  DevBuf d_diag_outs, d_diag_terms;
+  // Diagonal of H_eff: only channels that keep the sector (dq = 0, even parity) reach it,
+  // diag[l][r] = sum_{(a,b)} c_ab dL_a[l] dR_b[r] = sum_a dL_a[l] S_a[r] with
+  // S_a = sum_b c_ab dR_b per local pattern.  Work space (dg_buf): the diagonals of the
+  // dq = 0 blocks of L (one row of all bond-i states per channel) and of R, and S per
+  // pattern; dg_copy extracts the diagonals, dg_comb forms S, dg_gemm one product per psi
+  // block (K = number of such left channels).
+  std::vector<b2k::CopyTask> dg_copy;
+  DevBuf d_dg_copy;
+  CombProgram dg_comb;
+  GemmProgram dg_gemm;
+  int64_t dg_size = 0;
   DevBuf diag;              // the diagonal, computed on first use (environments are fixed)
   bool diag_done = false;
   bool comb_done = false;

@@ -244,31 +244,6 @@ void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const 
   g_launches += 1;
 }
 
-// ======================================================================== diagonal
-__global__ void __launch_bounds__(128) k_diag(const DiagOut* __restrict__ outs,
-                                              const DiagTerm* __restrict__ terms,
-                                              const double* __restrict__ L,
-                                              const double* __restrict__ R, double* diag) {
-  const DiagOut o = outs[blockIdx.x];
-  const int n = o.ml * o.mr;
-  for (int e = threadIdx.x; e < n; e += 128) {
-    int l = e / o.mr, r = e % o.mr;
-    double acc = 0.0;
-    for (int t = o.t0; t < o.t1; ++t) {
-      const DiagTerm d = terms[t];
-      acc = fma(d.c * L[d.offL + int64_t(l) * o.ml + l], R[d.offR + int64_t(r) * o.mr + r], acc);
-    }
-    diag[o.off + e] = acc;
-  }
-}
-
-void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
-                 const double* R, double* diag, cudaStream_t s) {
-  if (n_out <= 0) return;
-  k_diag<<<n_out, 128, 0, s>>>(outs, terms, L, R, diag);
-  g_launches += 1;
-}
-
 // =========================================================================== copy
 __global__ void __launch_bounds__(128) k_copy(const CopyTask* __restrict__ tasks, BufTable bt) {
   const CopyTask c = tasks[blockIdx.x];

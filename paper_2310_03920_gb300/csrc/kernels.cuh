@@ -71,18 +71,6 @@ struct CombTile {
   int64_t e0;
 };
 
-// diag block [ml x mr] (+)= sum_t c_t dL_t (x) dR_t, dL_t the diagonal of an ml x ml block,
-// dR_t the diagonal of an mr x mr block.
-struct DiagTerm {
-  int64_t offL, offR;
-  double c;
-};
-struct DiagOut {
-  int64_t off;
-  int ml, mr;
-  int t0, t1;
-};
-
 // Strided block copy: dst[r*ldd + c] = src[r*lds + c] (or src[c*lds + r] when trans).
 struct CopyTask {
   int64_t src, dst;
@@ -158,8 +146,6 @@ void launch_heff_tc(const TcGroup& g0, const TcGroup* groups, int n_groups, int 
                     int* status, uint32_t stuck_polls, cudaStream_t s);
 void launch_comb(const CombTile* tiles, int n_tiles, const CombOut* outs, const CombTerm* terms,
                  const BufTable& bt, cudaStream_t s);
-void launch_diag(int n_out, const DiagOut* outs, const DiagTerm* terms, const double* L,
-                 const double* R, double* diag, cudaStream_t s);
 void launch_copy(int n_tasks, const CopyTask* tasks, const BufTable& bt, cudaStream_t s);
 // Batched symmetric eigensolver (cyclic Jacobi); offs/eoffs: element offsets of each
 // matrix (dims^2 each) and of its eigenvalues; work/woffs: global work space of 2 dims^2
