@@ -151,8 +151,8 @@ class ClockSampler:
 
 
 def measured_peaks(torch):
-    """FP64 peak of this GPU (cuBLAS DGEMM through torch.matmul, 8192^3, best of 5) and the
-    measured HBM / bf16 figures."""
+    """FP64 and TF32 peaks of this GPU (cuBLAS through torch.matmul, 8192^3, float64 /
+    float32 with TF32 allowed, best of 5) and the measured HBM / bf16 figures."""
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -172,6 +172,23 @@ def measured_peaks(torch):
         torch.cuda.synchronize()
         best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
     peaks["fp64_tflops_measured"] = best
+    del a, b
+    # TF32: float32 matmul with TF32 tensor cores allowed (same protocol)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    a = torch.randn(n, n, dtype=torch.float32, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float32, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    peaks["tf32_tflops_measured"] = best
     del a, b
     torch.cuda.empty_cache()
     return peaks
