@@ -57,6 +57,8 @@ def parse():
                     help="skip the n=36 middle-window leg (products at M=1000/2000, Davidson "
                          "at M=1000 in FP64 and in split precision)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--window-m", type=int, default=0,
+                    help="window_M*: bond dimension of the n=36 window (default: from the name)")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "window_M1000", "window_M2000", "batch64", "grad_n24",
                              "eig_batch"],
@@ -325,6 +327,9 @@ def window_leg(b2, torch, ctx, M, davidson, reps, peaks):
         y = torch.empty_like(psi0)
         fl = b2.b2_heff_apply(ctx, env, c, psi0, y, prec=prec)   # builds / splits once
         ms = []
+        if prec == b2.B2_BF16X3:   # profiler range: the timed split-precision products
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
         for _ in range(1 if prec == b2.B2_FP64 else reps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -334,6 +339,8 @@ def window_leg(b2, torch, ctx, M, davidson, reps, peaks):
             e1.record(ctx.stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+        if prec == b2.B2_BF16X3:
+            torch.cuda.cudart().cudaProfilerStop()
         t = statistics.median(ms)
         ys[name] = y
         r = {"ms": t, "algo_flops": fl, "effective_tflops": fl / (t * 1e-3) / 1e12}
@@ -375,7 +382,7 @@ def run_window(args):
     split-precision product is the line's value; with --davidson also the window solves."""
     import torch
     from paper_2310_03920_gb300 import b2
-    M = 1000 if args.workload == "window_M1000" else 2000
+    M = args.window_m or (1000 if args.workload == "window_M1000" else 2000)
     ctx = b2.Context(0)
     peaks = measured_peaks(torch)
     b2.b2_profile(ctx, True)
@@ -717,21 +724,27 @@ def main():
         return
     peaks = measured_peaks(torch)
     fp64_peak = peaks["fp64_tflops_measured"]
-    def fp64_roofline(kernel, flops_, ms_, launches_):
+    # DRAM bytes per launch from one ncu capture of this sweep (dram__bytes_read.sum +
+    # dram__bytes_write.sum of the launches of one timed sweep): an eigensolver call = 192/61
+    # cluster launches of 0.35 MB + one one-CTA launch of 0.07 MB; k_gemm 0.83 MB
+    traffic = {"eig": 192.0 / 61.0 * 0.35e6 + 0.07e6, "k_gemm": 0.83e6}
+
+    def fp64_roofline(kernel, flops_, ms_, launches_, traffic_=None):
         ach = flops_ / (ms_ * 1e-3) / 1e12 if ms_ > 0 else 0.0
         return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak if fp64_peak else None,
                 "peak_source": "measured cuBLAS DGEMM 8192^3 on this GPU (FP64; not in "
                                "MEASURED_PEAKS.json)",
                 "launches": launches_, "avg_launch_us": ms_ * 1e3 / max(1, launches_),
-                "device_ms_per_step": ms_ / max(1, args.steps), "traffic": None}
+                "device_ms_per_step": ms_ / max(1, args.steps), "traffic": traffic_,
+                "traffic_unit": "bytes per launch (ncu capture of this workload)"}
 
     # the dominant kernel of the sweep (by device time) is reported as "roofline"
     rl_heff = fp64_roofline("k_gemm (H_eff block contraction, FP64)", prof["heff_flops"],
-                            prof["heff_ms"], prof["heff_launches"])
+                            prof["heff_ms"], prof["heff_launches"], traffic["k_gemm"])
     rl_eig = fp64_roofline("k_jacobi + k_jacobi_cluster (truncation eigensolver, FP64; "
                            "12 m_active + 6 m flops per applied rotation of an m x m block)",
-                           prof["eig_flops"], prof["eig_ms"], prof["eig_launches"])
+                           prof["eig_flops"], prof["eig_ms"], prof["eig_launches"], traffic["eig"])
     if prof["eig_ms"] > prof["heff_ms"]:
         roofline, roofline_other = rl_eig, rl_heff
     else:

@@ -797,7 +797,6 @@ void build_tc(Ctx* c, WindowProgram& wp) {
     to.accumulate = 1;
     to.t0 = int(tp.terms.size());
     double cst = 0;
-    int units16 = 0, units32 = 0;   // chain units with bf16 / tf32 chunks
     for (int t = o.t0; t < o.t1; ++t) {
       const GemmTerm& gt = g.terms[t];
       B2_REQUIRE((gt.flags & ~b2k::kBlockH) == kTransQ && gt.bufX == 0 && !o.accumulate,
@@ -818,15 +817,13 @@ void build_tc(Ctx* c, WindowProgram& wp) {
       tt.alpha = static_cast<float>(gt.alpha);
       tp.terms.push_back(tt);
       cst += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
-      units16 += (pad16(gt.K2) + 63) / 64;
-      units32 += (pad16(gt.K2) + 31) / 32;
     }
     to.t1 = int(tp.terms.size());
     tp.outs.push_back(to);
     if (to.t1 == to.t0) continue;   // nothing to add to the block-Hamiltonian part
     for (int r = 0; r < o.M; r += 128)
       for (int cc = 0; cc < o.N; cc += 128) {
-        tp.tiles.push_back({int(i), r, cc, {units16, units32}});
+        tp.tiles.push_back({int(i), r, cc});
         cost.push_back(cst);
       }
   }

@@ -128,7 +128,6 @@ struct TcTerm {   // 32 bytes: batches of them are copied into shared memory
 static_assert(sizeof(TcTerm) == 32, "TcTerm is moved in 16-byte units");
 struct TcTile {
   int out, r0, c0;
-  int units[2];   // chain units of the tile: bf16 (64-column chunks), tf32 (32-column chunks)
 };
 // One problem of a launch: tiles, outputs and terms, the split planes and the FP64 output;
 // tile0 is the grid index of its first tile (groups in increasing order).

@@ -54,7 +54,7 @@ constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo (follows the 
                                                      // inside shared memory)
 constexpr int kDynSmem = kRingBytes + 2 * kTpBytes + 1024;
 constexpr int kThreads = 320;                        // producer, MMA, 8 converter warps
-constexpr int kConvGroup = 128;                      // threads of one converter group (4 warps)
+constexpr int kConv = 256;                           // converter threads (8 warps)
 // TMEM columns: T0 [0,64), T1 [64,128), acc0 [128,256), acc1 [256,384)
 constexpr int kTmemCols = 512;
 // chain units summed in one FP32 accumulator before it is added to the FP64 output: bounds
@@ -95,6 +95,14 @@ __device__ __forceinline__ void mma(bool tf32, uint32_t tmem, uint64_t a, uint64
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
         "l"(a), "l"(b), "r"(id), "r"(accum));
+}
+
+// hi*hi + hi*lo + lo*hi of one K-step into tmem (descriptors of the hi and lo planes)
+__device__ __forceinline__ void mma3(bool tf32, uint32_t tmem, uint64_t ah, uint64_t al,
+                                     uint64_t bh, uint64_t bl, uint32_t id, uint32_t accum) {
+  mma(tf32, tmem, ah, bh, id, accum);
+  mma(tf32, tmem, ah, bl, id, 1u);
+  mma(tf32, tmem, al, bh, id, 1u);
 }
 
 __device__ __forceinline__ void commit(uint64_t* bar) {
@@ -315,16 +323,16 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     }
     for (int b = 0; b < 2; ++b) {
       bar_init(&tfull[b], 1);
-      bar_init(&tempty[b], kConvGroup);
-      bar_init(&tpready[b], kConvGroup);
+      bar_init(&tempty[b], kConv);
+      bar_init(&tpready[b], kConv);
       bar_init(&tpempty[b], 1);
       bar_init(&accfull[b], 1);
-      bar_init(&accempty[b], kConvGroup);
+      bar_init(&accempty[b], kConv);
       bar_init(&tbfull[b], 1);
     }
     for (int k = 0; k < kUnitRing; ++k) {
       bar_init(&ufull[k], 1);
-      bar_init(&uempty[k], kConvGroup);
+      bar_init(&uempty[k], kConv);
     }
     bar_init(&drainb, 1);
     bar_init(&neverb, 1);
@@ -441,9 +449,11 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       };
       issue_batch(0);
       if (n_batches > 1) issue_batch(1);
+      // item order: X(0), X(1), then X(u+2), Y(u): T of a unit is computed two units before
+      // its product with R, so the MMA thread never waits for a conversion to start the
+      // next T (two T buffers)
       uint32_t ui = 0;   // units produced
-      PendY pend{};
-      bool have_pend = false;
+      PendY pend[2] = {};
       for (int t = 0; t < n_terms && ok && !abort_flag; ++t) {
         TcTerm tm;
         if (!(ok = term(t, tm))) break;
@@ -483,14 +493,14 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
             ++item;
           }
           if (!ok) break;
-          // then the Y item of the previous unit (the MMA thread computes T of this unit
-          // before it multiplies the previous one by R)
-          if (have_pend && !(ok = produce_y(pend))) break;
-          pend = PendY{tm.offB2, int(tm.K2), c2, last_unit};
-          have_pend = true;
+          // then the Y item of the unit two back
+          if (ui >= 2 && !(ok = produce_y(pend[ui & 1]))) break;
+          pend[ui & 1] = PendY{tm.offB2, int(tm.K2), c2, last_unit};
         }
       }
-      if (ok && have_pend && !abort_flag) ok = produce_y(pend);
+      // the last two units' Y items
+      for (uint32_t u = ui >= 2 ? ui - 2 : 0; u < ui && ok && !abort_flag; ++u)
+        ok = produce_y(pend[u & 1]);
       // drain: every copy issued has landed before the CTA can exit (items already
       // consumed complete at once); the term batches too
       for (uint32_t i = oldest; i < item; ++i)
@@ -503,7 +513,9 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    // Items in the producer's order: the MMA1 chunks of unit u+1, then the MMA2 of unit u.
+    // Items in the producer's order.  Descriptors are formed once per item and stepped by
+    // 256 bytes (16 in descriptor units) per K-step: this single thread issues every MMA,
+    // so its instruction count per unit bounds the kernel.
     if (lane == 0) {
       uint32_t item = 0, ix = 0, iy = 0;
       bool ok = true;
@@ -512,6 +524,9 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         if (!bar_wait(&neverb, 0, stuck_polls, &abort_flag) && !abort_flag) fail();
         ok = false;
       }
+      const uint32_t id2 = idesc(n2, tf32);
+      const uint64_t tp0 = sdesc(smem_u32(tp_mem), 1024);   // T' buffer 0, hi plane
+      constexpr uint64_t kTpStep = uint64_t(kTpBytes) >> 4, kLoStep = uint64_t(kPBytes) >> 4;
       bool done = false;
       while (ok && !done) {
         const int s = int(item % kSlots);
@@ -533,13 +548,15 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t id1 = idesc(im.n1, tf32);
           const uint32_t tT = tmem + uint32_t(b * 64);
-          const uint32_t aH = st, aL = st + im.a, bH = st + 2 * im.a, bL = st + 2 * im.a + im.b;
-          for (int ks = 0; ks < im.kg / 2; ++ks) {
-            const uint32_t off = uint32_t(ks) * 256;
-            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bH + off, sbo), id1, (!im.first || ks > 0) ? 1u : 0u);
-            mma(tf32, tT, sdesc(aH + off, sbo), sdesc(bL + off, sbo), id1, 1u);
-            mma(tf32, tT, sdesc(aL + off, sbo), sdesc(bH + off, sbo), id1, 1u);
-          }
+          const uint64_t ah = sdesc(st, sbo), al = sdesc(st + im.a, sbo);
+          const uint64_t bh = sdesc(st + 2 * im.a, sbo), bl = sdesc(st + 2 * im.a + im.b, sbo);
+          const int kss = im.kg / 2;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            if (ks < kss) {
+              const uint64_t d = uint64_t(ks) * 16;
+              mma3(tf32, tT, ah + d, al + d, bh + d, bl + d, id1, (!im.first || ks > 0) ? 1u : 0u);
+            }
           commit(&empty[s]);
           if (im.last) {
             commit(&tfull[b]);
@@ -561,17 +578,16 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t tpH = smem_u32(tp_mem + b * kTpBytes), tpL = tpH + kPBytes;
           const uint32_t acc_tm = tmem + 128u + uint32_t(ab) * 128u;
-          const uint32_t id2 = idesc(n2, tf32);
-          const int ksteps = im.n1 * es / 32;
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t off = uint32_t(ks) * 256;
-            mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + off, sbo), id2,
-                (!gstart || ks > 0) ? 1u : 0u);
-            mma(tf32, acc_tm, sdesc(tpH + off, 1024), sdesc(st + im.a + off, sbo), id2, 1u);
-            mma(tf32, acc_tm, sdesc(tpL + off, 1024), sdesc(st + off, sbo), id2, 1u);
-          }
+          const uint64_t th = tp0 + uint64_t(b) * kTpStep, tl = th + kLoStep;
+          const uint64_t rh = sdesc(st, sbo), rl = sdesc(st + im.a, sbo);
+          const int kss = im.n1 * es / 32;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            if (ks < kss) {
+              const uint64_t d = uint64_t(ks) * 16;
+              mma3(tf32, acc_tm, th + d, tl + d, rh + d, rl + d, id2, (!gstart || ks > 0) ? 1u : 0u);
+            }
           commit(&empty[s]);
           commit(&tpempty[b]);
           if (im.last || iy % kGroup == kGroup - 1) commit(&accfull[ab]);
@@ -587,24 +603,22 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     __syncwarp();
   } else {
     // ------------------------------------------------------------ converter and flushes
-    // Two groups of 4 warps convert alternate chain units (group cg takes the units of its
-    // parity, T buffer and T' buffer cg), so two units are in conversion at once; warp w
-    // reads TMEM lane quarter w % 4 (tile rows 32 (w % 4) ..), one row per thread.  Warps
-    // whose rows all lie past the output block skip the arithmetic (their T' rows only feed
-    // accumulator rows that are never written).  Group 0 adds the accumulator groups to the
-    // FP64 output.
+    // 8 warps: warp w reads TMEM lane quarter w % 4 (tile rows), the two warps of a quarter
+    // take the two halves of the columns
     const int quad = warp & 3;
-    const int cg = (warp - 2) >> 2;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;       // tile row = TMEM lane
     const uint32_t lane_off = uint32_t(quad * 32) << 16;
-    const bool live = r0 + quad * 32 < o.M;
+    const int hw = wk / 2;                  // T columns per half (32 bf16, 16 tf32)
     const uint32_t rbase = uint32_t(row >> 3) * 1024 + uint32_t(row & 7) * 16;
-    const uint32_t n_units = uint32_t(tile.units[tf32 ? 1 : 0]);
     double* out = G.out + o.off;
     const int r = r0 + row;
+    // warps whose 32 rows all lie past the output block skip the arithmetic: their T' rows
+    // only feed accumulator rows that are never written
+    const bool live = r0 + quad * 32 < o.M;
     bool ok = true;
-    // add accumulator group g to the FP64 output (group 0 only); decisions are uniform over
-    // the warp (__all_sync) so that the warp-collective TMEM loads never run in part of it
+    // add accumulator group g to the FP64 output; every decision is uniform over the warp
+    // (__all_sync) so that the warp-collective TMEM loads never run in part of a warp
     auto flush = [&](uint32_t g) -> bool {
       const int ab = int(g & 1);
       if (!__all_sync(0xffffffffu, bar_wait(&accfull[ab], (g >> 1) & 1, limit, &abort_flag))) {
@@ -612,27 +626,28 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         return false;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int cb = 0; cb < n2 && live; cb += 64) {
-        uint32_t v[64];
+      uint32_t v[64];
+      const int cb = half * 64;
+      if (live) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (cb + 16 * j < n2) tmem_ld16_async(tmem + lane_off + 128u + uint32_t(ab) * 128u + uint32_t(cb + 16 * j), v + 16 * j);
         tmem_wait_ld();
-        if (r < o.M) {
-          double* p = out + int64_t(r) * o.N + c0 + cb;
-#pragma unroll
-          for (int j = 0; j < 64; ++j)
-            if (cb + j < n2 && c0 + cb + j < o.N) p[j] += double(__uint_as_float(v[j]));
-        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       bar_arrive(&accempty[ab]);
+      if (live && r < o.M) {
+        double* p = out + int64_t(r) * o.N + c0 + cb;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+          if (cb + j < n2 && c0 + cb + j < o.N) p[j] += double(__uint_as_float(v[j]));
+      }
       return true;
     };
-    unsigned char* tpH = tp_mem + cg * kTpBytes;
-    unsigned char* tpL = tpH + kPBytes;
-    for (uint32_t idx = uint32_t(cg); idx < n_units; idx += 2) {
-      const int b = cg;   // = idx & 1
+    uint32_t idx = 0;
+    bool last = false;
+    while (!last) {
+      const int b = idx & 1;
       const int k = int(idx % kUnitRing);
       bool w = bar_wait(&ufull[k], (idx / kUnitRing) & 1, limit, &abort_flag);
       if (w) w = bar_wait(&tfull[b], (idx >> 1) & 1, limit, &abort_flag);
@@ -645,59 +660,61 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const UnitMeta um = umeta[k];
       bar_arrive(&uempty[k]);
+      last = um.last != 0;
       const float alpha = um.alpha;
       const int n1 = um.n1;
-      uint32_t v[64];
+      const int cb = half * hw;
+      unsigned char* tpH = tp_mem + b * kTpBytes;
+      unsigned char* tpL = tpH + kPBytes;
+      uint32_t v[32];
       if (live) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (16 * j < wk && 16 * j < n1) tmem_ld16_async(tmem + lane_off + uint32_t(b * 64 + 16 * j), v + 16 * j);
+        for (int j = 0; j < 2; ++j)
+          if (16 * j < hw && cb + 16 * j < n1) tmem_ld16_async(tmem + lane_off + uint32_t(b * 64 + cb + 16 * j), v + 16 * j);
         tmem_wait_ld();
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       bar_arrive(&tempty[b]);   // T of this buffer is in registers
-      if (live) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cc = 16 * j;
-          if (cc >= wk || cc >= n1) continue;
-          if (tf32) {
+      for (int j = 0; j < 2; ++j) {
+        const int cc = cb + 16 * j;
+        if (!live || 16 * j >= hw || cc >= n1) continue;
+        if (tf32) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {   // 4 k-groups of 4 elements
-              uint32_t hh[4], ll[4];
+          for (int q = 0; q < 4; ++q) {   // 4 k-groups of 4 elements
+            uint32_t hh[4], ll[4];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) split_tf32(alpha * __uint_as_float(v[cc + 4 * q + e]), hh[e], ll[e]);
-              const uint32_t off = rbase + uint32_t((cc >> 2) + q) * 128;
-              *reinterpret_cast<uint4*>(tpH + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-              *reinterpret_cast<uint4*>(tpL + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
-            }
-          } else {
+            for (int e = 0; e < 4; ++e) split_tf32(alpha * __uint_as_float(v[16 * j + 4 * q + e]), hh[e], ll[e]);
+            const uint32_t off = rbase + uint32_t((cc >> 2) + q) * 128;
+            *reinterpret_cast<uint4*>(tpH + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4*>(tpL + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+          }
+        } else {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {   // 2 k-groups of 8 elements
-              uint16_t hh[8], ll[8];
+          for (int q = 0; q < 2; ++q) {   // 2 k-groups of 8 elements
+            uint16_t hh[8], ll[8];
 #pragma unroll
-              for (int e = 0; e < 8; ++e) split_bf16(alpha * __uint_as_float(v[cc + 8 * q + e]), hh[e], ll[e]);
-              const uint32_t off = rbase + uint32_t((cc >> 3) + q) * 128;
-              *reinterpret_cast<uint4*>(tpH + off) =
-                  make_uint4(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16),
-                             hh[4] | (uint32_t(hh[5]) << 16), hh[6] | (uint32_t(hh[7]) << 16));
-              *reinterpret_cast<uint4*>(tpL + off) =
-                  make_uint4(ll[0] | (uint32_t(ll[1]) << 16), ll[2] | (uint32_t(ll[3]) << 16),
-                             ll[4] | (uint32_t(ll[5]) << 16), ll[6] | (uint32_t(ll[7]) << 16));
-            }
+            for (int e = 0; e < 8; ++e) split_bf16(alpha * __uint_as_float(v[16 * j + 8 * q + e]), hh[e], ll[e]);
+            const uint32_t off = rbase + uint32_t((cc >> 3) + q) * 128;
+            *reinterpret_cast<uint4*>(tpH + off) =
+                make_uint4(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16),
+                           hh[4] | (uint32_t(hh[5]) << 16), hh[6] | (uint32_t(hh[7]) << 16));
+            *reinterpret_cast<uint4*>(tpL + off) =
+                make_uint4(ll[0] | (uint32_t(ll[1]) << 16), ll[2] | (uint32_t(ll[3]) << 16),
+                           ll[4] | (uint32_t(ll[5]) << 16), ll[6] | (uint32_t(ll[7]) << 16));
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(&tpready[b]);
-      // group 0: the accumulator group before this unit's is complete once its last unit's
-      // T' is handed over (kGroup is even, so the first unit of every group is group 0's)
-      if (cg == 0 && idx % kGroup == 0 && idx > 0 && !flush(idx / kGroup - 1)) {
+      // the group before this one is complete once this unit's T' is handed over
+      if (idx % kGroup == 0 && idx > 0 && !flush(idx / kGroup - 1)) {
         ok = false;
         break;
       }
+      ++idx;
     }
-    if (cg == 0 && ok && n_units > 0 && !flush((n_units - 1) / kGroup)) ok = false;
+    if (ok && idx > 0 && !flush((idx - 1) / kGroup)) ok = false;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
