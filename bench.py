@@ -60,15 +60,18 @@ def parse():
     ap.add_argument("--window-m", type=int, default=0,
                     help="window_M*: bond dimension of the n=36 window (default: from the name)")
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "window_M1000", "window_M2000", "batch64", "grad_n24",
-                             "eig_batch"],
+                    choices=["sweep", "window_M1000", "window_M2000", "batch64", "batch64_sweeps",
+                             "grad_n24", "eig_batch"],
                     help="sweep: Hubbard L=32 M=500 full sweep (default); window_M*: middle "
                          "window of the n=36 ab initio system, FP64 vs split precision; "
                          "batch64: 64 independent problems, grouped vs one-by-one launches; "
                          "grad_n24: integral gradient (1- and 2-RDM) at n=24, M=500; "
                          "eig_batch: the truncation eigensolver alone on one truncation-shaped "
                          "batch of graded density matrices")
-    ap.add_argument("--batch", type=int, default=64, help="problems of the batch64 workload")
+    ap.add_argument("--batch", type=int, default=64, help="problems of the batch64 workloads")
+    ap.add_argument("--sweeps", type=int, default=6, help="batch64_sweeps: sweeps per problem")
+    ap.add_argument("--one-by-one", action="store_true",
+                    help="batch64_sweeps: also run every problem's sweeps one problem at a time")
     ap.add_argument("--davidson", action="store_true",
                     help="window_M*: also solve the window (split precision to |r|^2 <= 1e-7, "
                          "then FP64 from that vector) and report |dE|; several minutes")
@@ -507,6 +510,86 @@ def run_batch(args):
     ctx.close()
 
 
+def run_batch_sweeps(args):
+    """All problems of the batch (synth.batch_problem: Hubbard L in [12, 40], U in [1, 8];
+    ab initio n in [10, 24]; M in [100, 800]) run to the end of --sweeps two-site sweeps at
+    their own bond dimension, from random MPS (b2_mps_random, seed of the problem) in
+    lockstep (b2_sweep_batched_dims: one grouped H_eff launch per Davidson iteration over
+    every problem still iterating).  value = the problems' H_eff flops / time to all done."""
+    import numpy as np
+    import torch
+    from paper_2310_03920_gb300 import b2
+    from synth import batch_problem
+    ctx = b2.Context(0)
+    probs = []
+    t0 = time.perf_counter()
+    for j in range(args.batch):
+        pr = batch_problem(j)
+        n, N, tsz = pr["n"], pr["n_elec"], pr["two_sz"]
+        occ = np.full(n, 0.5) if pr["kind"] == "hubbard" else None
+        mpo = b2.b2_build_mpo(ctx, pr["h"], pr["eri"], 0.0, N, tsz)
+        probs.append({"mpo": mpo, "occ": occ, "seed": pr["seed"], "M": pr["M"], "n": n,
+                      "kind": pr["kind"]})
+    t_mpo = time.perf_counter() - t0
+
+    def fresh():
+        envs = []
+        for p in probs:
+            p["mps"] = b2.b2_mps_random(ctx, p["mpo"], p["M"], p["occ"], p["seed"])
+            envs.append(b2.b2_env_init(ctx, p["mpo"], p["mps"], 0))
+        return envs
+
+    def release(envs):
+        for p, e in zip(probs, envs):
+            b2.b2_free_env(e)
+            b2.b2_free_mps(p["mps"])
+
+    dims = [[p["M"]] * args.sweeps for p in probs]
+    envs = fresh()
+    torch.cuda.synchronize()
+    b2.b2_profile(ctx, True)
+    t0 = time.perf_counter()
+    res = b2.b2_sweep_batched_dims(ctx, envs, dims)
+    torch.cuda.synchronize()
+    t_lock = time.perf_counter() - t0
+    prof = b2.b2_profile_read(ctx)
+    b2.b2_profile(ctx, False)
+    flops = sum(r["matvec_flops"] for pr in res for r in pr)
+    energies = [pr[-1]["energy"] for pr in res]
+    release(envs)
+    out = {"lockstep_s": t_lock, "lockstep_tflops": flops / t_lock / 1e12,
+           "heff_device_ms": prof["heff_ms"], "eig_device_ms": prof["eig_ms"],
+           "gpu_launches": int(prof["launches"])}
+    if args.one_by_one:
+        envs = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e1 = []
+        for p, e in zip(probs, envs):
+            r = b2.b2_sweep(ctx, p["mpo"], p["mps"], e, [p["M"]] * args.sweeps)
+            e1.append(r[-1]["energy"])
+        torch.cuda.synchronize()
+        out["one_by_one_s"] = time.perf_counter() - t0
+        out["speedup"] = out["one_by_one_s"] / t_lock
+        out["energies_identical"] = all(a == b for a, b in zip(energies, e1))
+        release(envs)
+    line = {"metric": METRIC, "value": out["lockstep_tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": t_lock * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch%d_%dsweeps_lockstep" % (len(probs), args.sweeps),
+                       "problems": len(probs),
+                       "hubbard": sum(p["kind"] == "hubbard" for p in probs),
+                       "ab_initio": sum(p["kind"] != "hubbard" for p in probs),
+                       "n_range": [min(p["n"] for p in probs), max(p["n"] for p in probs)],
+                       "M_range": [min(p["M"] for p in probs), max(p["M"] for p in probs)]},
+            "batch": out, "mpo_build_s": t_mpo,
+            "final_energies": {"min": min(energies), "max": max(energies)}}
+    print(json.dumps(line), flush=True)
+    for p in probs:
+        b2.b2_free_mpo(p["mpo"])
+    ctx.close()
+
+
 def run_grad(args):
     """Integral gradient dE/dh, dE/d(pq|rs) (spin-traced 1- and 2-RDM) of an n = 24,
     N = 24 ab initio MPS at M = 500 (random MPS from the sector recipe, seeded): times
@@ -608,6 +691,9 @@ def main():
         return
     if args.workload == "batch64":
         run_batch(args)
+        return
+    if args.workload == "batch64_sweeps":
+        run_batch_sweeps(args)
         return
     if args.workload == "grad_n24":
         run_grad(args)

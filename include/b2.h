@@ -240,6 +240,10 @@ int b2_davidson_batched(b2_ctx ctx, int n, const b2_env* envs, const int* sites,
                         int* n_matvec, double* resid2);
 int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts* opts,
                      b2_sweep_result* results);
+/* b2_sweep_batched with a bond dimension per problem and sweep: bond_dims (host,
+ * n * opts->n_sweeps ints, problem-major) replaces opts->bond_dims (which may be NULL). */
+int b2_sweep_batched_dims(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts* opts,
+                          const int* bond_dims, b2_sweep_result* results);
 
 /* ------------------------------------------------------------------ batched eigensolver
  * Eigen-decomposition of n_mat real symmetric matrices by cyclic Jacobi rotations in

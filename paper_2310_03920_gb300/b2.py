@@ -76,6 +76,7 @@ _sig = {
     "b2_heff_apply_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_d)]),
     "b2_davidson_batched": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(DavOpts), _vp, _vp, _vp]),
     "b2_sweep_batched": (_i, [_vp, _i, _vp, ctypes.POINTER(SweepOpts), _vp]),
+    "b2_sweep_batched_dims": (_i, [_vp, _i, _vp, ctypes.POINTER(SweepOpts), _vp, _vp]),
     "b2_debug_limits": (_i, [_vp, _i, _i]),
     "b2_sync": (_i, [_vp]),
     "b2_profile": (_i, [_vp, _i]),
@@ -337,6 +338,21 @@ def b2_sweep_batched(ctx, envs, bond_dims, conv_tol=1e-10, dav_max_iter=30, max_
     res = (SweepResult * (n * len(bond_dims)))()
     _check(ctx.h, lib.b2_sweep_batched(ctx.h, n, _handles(envs), ctypes.byref(o), res))
     k = len(bond_dims)
+    return [[{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res[p * k:(p + 1) * k]]
+            for p in range(n)]
+
+
+def b2_sweep_batched_dims(ctx, envs, bond_dims, conv_tol=1e-10, dav_max_iter=30,
+                          max_subspace=30, prec=B2_FP64, trunc_cutoff=1e-14):
+    """bond_dims: one list of per-sweep bond dimensions per problem (equal lengths)."""
+    n = len(envs)
+    k = len(bond_dims[0])
+    assert all(len(b) == k for b in bond_dims)
+    flat = np.ascontiguousarray(np.array(bond_dims, dtype=np.int32).reshape(-1))
+    o = SweepOpts(k, None, conv_tol, dav_max_iter, max_subspace, prec, trunc_cutoff)
+    res = (SweepResult * (n * k))()
+    _check(ctx.h, lib.b2_sweep_batched_dims(ctx.h, n, _handles(envs), ctypes.byref(o),
+                                            flat.ctypes.data, res))
     return [[{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res[p * k:(p + 1) * k]]
             for p in range(n)]
 

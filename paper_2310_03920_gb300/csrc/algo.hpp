@@ -36,7 +36,7 @@ std::vector<DavidsonResult> davidson_batched(Ctx* c, const std::vector<b2_env_s*
                                              const std::vector<double*>& psis,
                                              const b2_dav_opts& o);
 void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_opts& o,
-                   b2_sweep_result* res);
+                   b2_sweep_result* res, const int* dims_per_problem = nullptr);
 // Integral gradient (spin-traced 1- and 2-particle density matrices) of the MPS energy;
 // host outputs, see b2_rdm_grad.
 void rdm_grad(Ctx* c, b2_mpo_s* mpo, b2_mps_s* mps, double* h1_grad, double* eri_grad);

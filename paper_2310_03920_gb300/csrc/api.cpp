@@ -365,6 +365,20 @@ int b2_sweep_batched(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts*
   });
 }
 
+int b2_sweep_batched_dims(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_opts* opts,
+                          const int* bond_dims, b2_sweep_result* results) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(n >= 0, B2_EINVAL, "n < 0");
+    if (n == 0) return;
+    B2_REQUIRE(envs && opts && bond_dims && opts->n_sweeps >= 0, B2_EINVAL,
+               "bad batched sweep arguments");
+    for (int i = 0; i < n; ++i) check_env(ctx, envs[i]);
+    ensure_device(ctx);
+    std::vector<b2_env_s*> e(envs, envs + n);
+    b2::sweep_batched(&ctx->c, e, *opts, results, bond_dims);
+  });
+}
+
 int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri_grad) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx && mpo && mps && h1_grad && eri_grad, B2_EINVAL, "null argument");

@@ -343,7 +343,7 @@ std::vector<DavidsonResult> davidson_batched(Ctx* c, const std::vector<b2_env_s*
 // split of the single-problem sweep.  Results per problem and sweep; seconds = wall time
 // of the whole batch's sweep.
 void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_opts& o,
-                   b2_sweep_result* res) {
+                   b2_sweep_result* res, const int* dims_per_problem) {
   const int np = int(envs.size());
   b2_dav_opts dop;
   dop.max_iter = o.dav_max_iter > 0 ? o.dav_max_iter : 30;
@@ -373,8 +373,11 @@ void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_op
   for (int sw = 0; sw < o.n_sweeps; ++sw) {
     B2_CUDA(cudaStreamSynchronize(c->stream));
     const auto t0 = std::chrono::steady_clock::now();
-    const int M = o.bond_dims[sw];
-    B2_REQUIRE(M >= 1, B2_EINVAL, "bond dimension must be positive");
+    std::vector<int> Mp(np);
+    for (int p = 0; p < np; ++p) {
+      Mp[p] = dims_per_problem ? dims_per_problem[size_t(p) * o.n_sweeps + sw] : o.bond_dims[sw];
+      B2_REQUIRE(Mp[p] >= 1, B2_EINVAL, "bond dimension must be positive");
+    }
     std::vector<b2_sweep_result> r(np);
     double t_dav = 0, t_split = 0;
     for (int t = 0; t < max_steps; ++t) {
@@ -403,9 +406,9 @@ void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_op
         r[p].energy = d[j].energy;
         double dw = 0;
         if (t <= n - 2) {
-          if (i < n - 2) split_left(envs[p], i, psi[p], M, cutoff, &dw, &r[p].other_flops);
+          if (i < n - 2) split_left(envs[p], i, psi[p], Mp[p], cutoff, &dw, &r[p].other_flops);
         } else if (i > 0) {
-          split_right(envs[p], i, psi[p], M, cutoff, &dw, &r[p].other_flops, true);
+          split_right(envs[p], i, psi[p], Mp[p], cutoff, &dw, &r[p].other_flops, true);
         }
         r[p].discarded_weight = std::max(r[p].discarded_weight, dw);
       }
