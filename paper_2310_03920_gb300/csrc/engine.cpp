@@ -816,13 +816,13 @@ void build_tc(Ctx* c, WindowProgram& wp) {
       tt.K2 = uint16_t(gt.K2);
       tt.alpha = static_cast<float>(gt.alpha);
       tp.terms.push_back(tt);
-      cst += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, 128)));
+      cst += double(pad16(gt.K2)) * (pad16(gt.K1) + pad16(std::min(o.N, b2k::kTcTileN)));
     }
     to.t1 = int(tp.terms.size());
     tp.outs.push_back(to);
     if (to.t1 == to.t0) continue;   // nothing to add to the block-Hamiltonian part
-    for (int r = 0; r < o.M; r += 128)
-      for (int cc = 0; cc < o.N; cc += 128) {
+    for (int r = 0; r < o.M; r += b2k::kTcTileM)
+      for (int cc = 0; cc < o.N; cc += b2k::kTcTileN) {
         tp.tiles.push_back({int(i), r, cc});
         cost.push_back(cst);
       }

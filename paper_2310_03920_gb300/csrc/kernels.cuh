@@ -126,6 +126,9 @@ struct TcTerm {   // 32 bytes: batches of them are copied into shared memory
   float alpha;
 };
 static_assert(sizeof(TcTerm) == 32, "TcTerm is moved in 16-byte units");
+// Output tiles of the tensor-core contraction: kTcTileM rows x kTcTileN columns of a psi
+// block (two CTAs per SM).
+constexpr int kTcTileM = 64, kTcTileN = 64;
 struct TcTile {
   int out, r0, c0;
 };

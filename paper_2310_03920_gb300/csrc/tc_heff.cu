@@ -47,16 +47,22 @@ namespace {
 // MMA group reads: L and psi^T for MMA1, R for MMA2, hi and lo planes) takes exactly its
 // size, so many small blocks are in flight at once; at most kSlots items are outstanding.
 constexpr int kSlots = 16;
-constexpr int kRingBytes = 152 * 1024;
+// Two CTAs per SM (two MMA-issuing threads): an output tile is kTcTileM x kTcTileN (the
+// MMAs keep M = 128; accumulator rows past the tile are discarded)
+constexpr int kTileM = kTcTileM, kTileN = kTcTileN;
 constexpr int kPBytes = 128 * 128;                   // 128 rows x one 128-byte K chunk
 constexpr int kTpBytes = 2 * kPBytes;                // T' hi + lo (follows the ring: an A
                                                      // operand read past its item's rows stays
                                                      // inside shared memory)
+constexpr int kRingBytes = 40 * 1024;
 constexpr int kDynSmem = kRingBytes + 2 * kTpBytes + 1024;
-constexpr int kThreads = 320;                        // producer, MMA, 8 converter warps
-constexpr int kConv = 256;                           // converter threads (8 warps)
-// TMEM columns: T0 [0,64), T1 [64,128), acc0 [128,256), acc1 [256,384)
-constexpr int kTmemCols = 512;
+// warps: 2 producer, 3 MMA issuer, 0 1 4 5 converters (TMEM lane quarters 0 and 1 hold the
+// tile's rows; the two warps of a quarter take the two halves of the columns)
+constexpr int kThreads = 192;
+constexpr int kProducerWarp = 2, kMmaWarp = 3;
+constexpr int kConv = 128;                           // converter threads (4 warps)
+// TMEM columns: T0 [0,64), T1 [64,128), acc0 [128,192), acc1 [192,256)
+constexpr int kTmemCols = 256;
 // chain units summed in one FP32 accumulator before it is added to the FP64 output: bounds
 // the FP32 rounding error of the long term sums (thousands of terms per output block)
 constexpr int kGroup = 16;
@@ -311,9 +317,9 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
   const int wk = 128 / es;   // elements in one 128-byte K chunk (= T columns per unit)
   const TcOut o = G.outs[tile.out];
   const int r0 = tile.r0, c0 = tile.c0;
-  const int n2 = pad16(min(128, o.N - c0));           // MMA2 N (acc columns)
-  const int rowsA = min(128, pad16(o.M) - r0);        // L rows loaded for this tile
-  const int rowsB2 = min(128, pad16(o.N) - c0);       // R rows loaded for this tile
+  const int n2 = pad16(min(kTileN, o.N - c0));        // MMA2 N (acc columns)
+  const int rowsA = min(kTileM, pad16(o.M) - r0);     // L rows loaded for this tile
+  const int rowsB2 = min(kTileN, pad16(o.N) - c0);    // R rows loaded for this tile
   const uint32_t limit = kDefaultWait;
 
   if (tid == 0) {
@@ -339,7 +345,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
                  "r"(kTmemCols));
@@ -357,7 +363,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
   auto nchunks = [&](int k) { return (pad16(k) * es + 127) / 128; };
   const int n_terms = o.t1 - o.t0;
 
-  if (warp == 0) {
+  if (warp == kProducerWarp) {
     // ------------------------------------------------------------ producer
     // The only role that reads the term list: batches of kTermBatch terms are copied into
     // shared memory two ahead; every item carries what the MMA thread needs (imeta), every
@@ -412,6 +418,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         while (item - oldest >= uint32_t(kSlots))
           if (!retire()) return false;
         for (;;) {
+          if (oldest == item) head = 0;   // empty ring: start at 0, so any item fits
           const bool fits = head + sz <= uint32_t(kRingBytes);
           const uint32_t fp = fits ? sz : (uint32_t(kRingBytes) - head) + sz;
           if (fp <= uint32_t(kRingBytes) - used) {
@@ -422,7 +429,10 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
             head = pos + sz;
             return true;
           }
-          if (!retire()) return false;
+          if (oldest == item || !retire()) {   // (an item never exceeds the ring)
+            if (!abort_flag) fail();
+            return false;
+          }
         }
       };
       // Y item of a unit (R chunk), from the values kept when its X items were produced
@@ -511,7 +521,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     // Items in the producer's order.  Descriptors are formed once per item and stepped by
     // 256 bytes (16 in descriptor units) per K-step: this single thread issues every MMA,
@@ -578,7 +588,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t acc_tm = tmem + 128u + uint32_t(ab) * 128u;
+          const uint32_t acc_tm = tmem + 128u + uint32_t(ab * kTileN);
           const uint64_t th = tp0 + uint64_t(b) * kTpStep, tl = th + kLoStep;
           const uint64_t rh = sdesc(st, sbo), rl = sdesc(st + im.a, sbo);
           const int kss = im.n1 * es / 32;
@@ -603,10 +613,10 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
     __syncwarp();
   } else {
     // ------------------------------------------------------------ converter and flushes
-    // 8 warps: warp w reads TMEM lane quarter w % 4 (tile rows), the two warps of a quarter
-    // take the two halves of the columns
+    // warp w reads TMEM lane quarter w % 4 (tile rows 32 (w % 4) ..), the two warps of a
+    // quarter take the two halves of the columns
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = warp >> 2;
     const int row = quad * 32 + lane;       // tile row = TMEM lane
     const uint32_t lane_off = uint32_t(quad * 32) << 16;
     const int hw = wk / 2;                  // T columns per half (32 bf16, 16 tf32)
@@ -626,12 +636,13 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
         return false;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t v[64];
-      const int cb = half * 64;
+      constexpr int kHalfN = kTileN / 2;
+      uint32_t v[kHalfN];
+      const int cb = half * kHalfN;
       if (live) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (cb + 16 * j < n2) tmem_ld16_async(tmem + lane_off + 128u + uint32_t(ab) * 128u + uint32_t(cb + 16 * j), v + 16 * j);
+        for (int j = 0; j < kHalfN / 16; ++j)
+          if (cb + 16 * j < n2) tmem_ld16_async(tmem + lane_off + 128u + uint32_t(ab * kTileN + cb + 16 * j), v + 16 * j);
         tmem_wait_ld();
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -639,7 +650,7 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
       if (live && r < o.M) {
         double* p = out + int64_t(r) * o.N + c0 + cb;
 #pragma unroll
-        for (int j = 0; j < 64; ++j)
+        for (int j = 0; j < kHalfN; ++j)
           if (cb + j < n2 && c0 + cb + j < o.N) p[j] += double(__uint_as_float(v[j]));
       }
       return true;
@@ -718,13 +729,13 @@ __device__ __forceinline__ void heff_tc_tile(const TcGroup& G, const TcTile tile
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1)
+  if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // One problem (g0, passed by value) or several (groups in device memory): CTA b takes tile
 // b - tile0 of the group g with tile0(g) <= b < tile0(g + 1).
-__global__ void __launch_bounds__(kThreads, 1) k_heff_tc(const __grid_constant__ TcGroup g0,
+__global__ void __launch_bounds__(kThreads, 2) k_heff_tc(const __grid_constant__ TcGroup g0,
                                                           const TcGroup* __restrict__ groups,
                                                           int n_groups, int* status,
                                                           uint32_t stuck_polls, int tf32) {
