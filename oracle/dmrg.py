@@ -189,6 +189,49 @@ class Heff:
         return d.reshape(ml, 4, 4, mr)
 
 
+class Heff1:
+    """H_eff of the one-site window of site i from L_i, R_{i+1} and the MPO (Sec. 2.1.2,
+    one-site algorithm: the d = 4 space of one site between the two blocks).
+
+    Applied to psi (M_i, 4, M_{i+1}): Y = sum_{a,b} (L_a P^{p(a)}) (x) O'_ab (x) R_b with
+    O_ab = W_i[a, b] and O'_ab = O_ab diag((-1)^{p(b) n(s)}), the sign of moving the right
+    part past the site ket (the two-site rule with one site)."""
+
+    def __init__(self, mpo, i, L, R, lab_l):
+        self.L, self.R = L, R
+        self.par_l = parity_of(lab_l)
+        self.pa = mpo.parity[i]
+        self.pb = mpo.parity[i + 1]
+        self.sgn_in = np.where(ops.SITE_N % 2 == 1, -1.0, 1.0)
+        self.terms = {}
+        for (a, b), m in mpo.W[i].items():
+            if np.any(m):
+                self.terms[(a, b)] = m * self.sgn_in[None, :] if self.pb[b] else m
+
+    def apply(self, psi):
+        ml, _, mr = psi.shape
+        x = psi.reshape(ml, 4 * mr)
+        y = np.zeros(psi.shape)
+        by_a = {}
+        for (a, b), o in self.terms.items():
+            by_a.setdefault(a, []).append((b, o))
+        for a, lst in by_a.items():
+            La = self.L[a] * self.par_l[None, :] if self.pa[a] else self.L[a]
+            t = (La @ x).reshape(ml, 4, mr)                       # L_a psi
+            for b, o in lst:
+                # y[l', s', r'] += sum_{s, r} o[s', s] t[l', s, r] R_b[r', r]
+                y += np.einsum("uv,xvr->xur", o, t) @ self.R[b].T
+        return y
+
+    def diag(self):
+        ml, mr = self.L[0].shape[0], self.R[0].shape[0]
+        d = np.zeros((ml, 4, mr))
+        for (a, b), o in self.terms.items():
+            dl = np.diag(self.L[a]) * (self.par_l if self.pa[a] else 1.0)
+            d += dl[:, None, None] * np.diag(o)[None, :, None] * np.diag(self.R[b])[None, None, :]
+        return d
+
+
 # ------------------------------------------------------------------------------ Davidson
 def davidson(matvec, diag, x0, tol=1e-10, max_iter=30, max_sub=30):
     """Lowest eigenpair by the standard Davidson method (Davidson 1975).
@@ -320,6 +363,50 @@ def right_split(psi, lab_r, M, cutoff=1e-14):
     return B, C, np.array(lab, dtype=np.int64).reshape(-1, 2), total - keptw
 
 
+def left_split1(psi, lab_l, M, cutoff=1e-14):
+    """One-site psi (l s, r) -> A (l, s, new) with A^T A = 1, C = A^T psi (new, r), new
+    bond labels, discarded weight (the density matrix of the left part, as left_split)."""
+    ml, _, mr = psi.shape
+    X = psi.reshape(ml * 4, mr)
+    row_lab = (lab_l[:, None, :] + SITE_Q[None, :, :]).reshape(-1, 2)
+    eig = _sector_eigs(X, row_lab)
+    kept = _select([e[2] for e in eig], M, cutoff)
+    cols, lab = [], []
+    for (q, rows, w, u), kq in zip(eig, kept):
+        for t in range(kq):
+            c = np.zeros(ml * 4)
+            c[rows] = u[:, t]
+            cols.append(c)
+            lab.append(q)
+    U = np.array(cols).T
+    total = sum(float(np.sum(e[2])) for e in eig)
+    keptw = sum(float(np.sum(e[2][:kq])) for e, kq in zip(eig, kept))
+    return (U.reshape(ml, 4, -1), U.T @ X, np.array(lab, dtype=np.int64).reshape(-1, 2),
+            total - keptw)
+
+
+def right_split1(psi, lab_r, M, cutoff=1e-14):
+    """One-site psi (l, s r) -> B (new, s, r) with B B^T = 1, C = psi B^T (l, new), new
+    bond labels (left-block quantum numbers), discarded weight."""
+    ml, _, mr = psi.shape
+    X = psi.reshape(ml, 4 * mr)
+    col_lab = (lab_r[None, :, :] - SITE_Q[:, None, :]).reshape(-1, 2)
+    eig = _sector_eigs(X.T, col_lab)
+    kept = _select([e[2] for e in eig], M, cutoff)
+    rows_out, lab = [], []
+    for (q, cidx, w, u), kq in zip(eig, kept):
+        for t in range(kq):
+            r = np.zeros(4 * mr)
+            r[cidx] = u[:, t]
+            rows_out.append(r)
+            lab.append(q)
+    Bm = np.array(rows_out)
+    total = sum(float(np.sum(e[2])) for e in eig)
+    keptw = sum(float(np.sum(e[2][:kq])) for e, kq in zip(eig, kept))
+    return (Bm.reshape(-1, 4, mr), X @ Bm.T, np.array(lab, dtype=np.int64).reshape(-1, 2),
+            total - keptw)
+
+
 # --------------------------------------------------------------------------------- sweep
 class DMRG:
     """Two-site DMRG driver.  Sweep = forward half over windows 0..n-2 followed by a
@@ -387,9 +474,87 @@ class DMRG:
                 dws.append(self.move_left(i, M, cutoff))
         return e, max(dws) if dws else 0.0
 
-    def run(self, bond_dims, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+    def run(self, bond_dims, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14, dots=None):
+        """Sweeps with bond dimension bond_dims[k]; dots[k] = 1 makes sweep k a one-site
+        sweep (default: all two-site).  Mixing the two (Sec. 2.1.2) switches between the
+        two-site and the one-site wavefunction at the start of a sweep."""
         energies = []
-        for M in bond_dims:
-            e, _ = self.sweep(M, tol, max_iter, max_sub, cutoff)
+        for k, M in enumerate(bond_dims):
+            if dots is not None and dots[k] == 1:
+                e, _ = self.sweep1(M, tol, max_iter, max_sub, cutoff)
+            else:
+                self.to_two_site()
+                e, _ = self.sweep(M, tol, max_iter, max_sub, cutoff)
             energies.append(e)
         return energies
+
+    # ------------------------------------------------------------ one-site algorithm
+    # Between sweeps the centre is at the left end: either the two-site psi of window
+    # (0, 1) (after a two-site sweep; R_2 exists) or the one-site psi of site 0 (after a
+    # one-site sweep or at the start; R_1 exists once needed).
+    def heff1(self, i):
+        return Heff1(self.mpo, i, self.L[i], self.R[i + 1], self.lab[i])
+
+    def to_one_site(self, M, cutoff):
+        """Two-site psi of window (0, 1) -> one-site psi of site 0 by the backward split
+        (B_1 right-orthonormal, R_1 from it), truncated like any split to M states.  At the
+        start (no sweep yet) the centre tensor A_0 itself is the one-site psi."""
+        if self.psi.ndim == 3:
+            return
+        if not self.stats:
+            self.psi = self.A[0].copy()
+        else:
+            B, C, lab, _ = right_split(self.psi, self.lab[2], M, cutoff)
+            self.A[1] = B
+            self.lab[1] = lab
+            self.psi = C.reshape(C.shape[0], 4, -1)
+        self.R[1] = right_env_update(self.R[2], self.A[1], self.mpo.W[1], self.mpo.parity[2],
+                                     len(self.mpo.chans[1]))
+
+    def to_two_site(self):
+        """One-site psi of site 0 -> two-site psi of window (0, 1): psi . A_1."""
+        if self.psi.ndim == 3:
+            self.psi = np.einsum("asb,btc->astc", self.psi, self.A[1])
+
+    def optimise1(self, i, tol, max_iter, max_sub):
+        h = self.heff1(i)
+        e, psi, nmv, rn2 = davidson(h.apply, h.diag(), self.psi, tol, max_iter, max_sub)
+        self.psi = psi
+        self.stats.append({"window": i, "energy": e, "n_matvec": nmv, "resid2": rn2, "dot": 1})
+        return e
+
+    def move_right1(self, i, M, cutoff):
+        A, C, lab, dw = left_split1(self.psi, self.lab[i], M, cutoff)
+        self.A[i] = A
+        self.lab[i + 1] = lab
+        self.L[i + 1] = left_env_update(self.L[i], A, self.mpo.W[i], self.lab[i],
+                                        len(self.mpo.chans[i + 1]))
+        self.psi = np.einsum("ab,bsc->asc", C, self.A[i + 1])
+        return dw
+
+    def move_left1(self, i, M, cutoff):
+        B, C, lab, dw = right_split1(self.psi, self.lab[i + 1], M, cutoff)
+        self.A[i] = B
+        self.lab[i] = lab
+        self.R[i] = right_env_update(self.R[i + 1], B, self.mpo.W[i], self.mpo.parity[i + 1],
+                                     len(self.mpo.chans[i]))
+        self.psi = np.einsum("asb,bc->asc", self.A[i - 1], C)
+        return dw
+
+    def sweep1(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+        """One-site sweep: forward over sites 0..n-1 (left split and move right after each
+        site but the last), backward over sites n-1..0 (right split and move left after
+        each site but site 0).  Without noise a split can keep at most the rank of psi's
+        matricisation, so bond dimensions never grow."""
+        n = self.n
+        self.to_one_site(M, cutoff)
+        dws = []
+        for i in range(0, n):
+            self.optimise1(i, tol, max_iter, max_sub)
+            if i < n - 1:
+                dws.append(self.move_right1(i, M, cutoff))
+        for i in range(n - 1, -1, -1):
+            e = self.optimise1(i, tol, max_iter, max_sub)
+            if i > 0:
+                dws.append(self.move_left1(i, M, cutoff))
+        return e, max(dws) if dws else 0.0

@@ -120,16 +120,18 @@ class MPO:
 
     def dense(self):
         """Dense 4^n x 4^n matrix (site 0 most significant), for small n only."""
-        T = {0: np.ones((1, 1))}
+        import scipy.sparse as sp   # the same Kronecker products, stored sparse
+        T = {0: sp.csr_matrix(np.ones((1, 1)))}
         for k in range(self.n):
             new = {}
             for (w, w2), m in self.W[k].items():
                 if w not in T:
                     continue
                 mp = m @ ops.PARITY if self.parity[k + 1][w2] else m
-                new[w2] = new.get(w2, 0.0) + np.kron(T[w], mp)
+                t = sp.kron(T[w], sp.csr_matrix(mp), format="csr")
+                new[w2] = new[w2] + t if w2 in new else t
             T = new
-        return T[self.chans[self.n]["H"]]
+        return T[self.chans[self.n]["H"]].toarray()
 
 
 def product_state_dets(n):
