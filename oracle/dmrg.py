@@ -277,6 +277,80 @@ def davidson(matvec, diag, x0, tol=1e-10, max_iter=30, max_sub=30):
     return theta, u.reshape(shape), nmv, rn2
 
 
+# ------------------------------------------------------------------ perturbative noise
+# The MPO factorises exactly across the bond being split (channels w of that bond):
+#   H = sum_w S_w (x) E_w,  S_w = sum_a (-1)^{p(a) N(l)} L_a (x) W_left[a, w] diag((-1)^{p(w) n(s)}),
+#                           E_w = sum_b W_right[w, b] diag((-1)^{p(b) n(s)}) (x) R_b,
+# (the two-site H_eff's signs regrouped: the sign of moving the right part of w past the
+# left site is (-1)^{p(w) n(s1)}).  The perturbative noise of White (2005) adds to the
+# density matrix of the kept part the weight that the system-side operators move psi into:
+# N = sum_w P_w P_w^T with P_w = S_w psi (forward split, kept part (l, s)) or E_w psi
+# (backward split, kept part (s, r)); sign factors on the other side's indices cancel in
+# P_w P_w^T.  The split then diagonalises rho + noise * N / tr N (N restricted to the
+# sectors the new bond can hold), so the noise adds total weight `noise` (Sec. 2.1.6 names
+# perturbative noise; the normalisation is this build's choice).
+def system_left(X3, L, W, par_l, pa, pw):
+    """{w: P_w = S_w psi} for X3 = psi as (M_l, 4, cols), rows (l, s) the kept part.  W: the
+    MPO tensor of the kept site, channels (a on the left bond, w on the cut bond); pw: the
+    parities of the cut bond's channels."""
+    ml, _, nc = X3.shape
+    sgn = np.where(ops.SITE_N % 2 == 1, -1.0, 1.0)
+    P = {}
+    for (a, w), m in W.items():
+        La = L[a] * par_l[None, :] if pa[a] else L[a]
+        mw = m * sgn[None, :] if pw[w] else m
+        t = (La @ X3.reshape(ml, 4 * nc)).reshape(ml, 4, nc)       # L_a psi
+        t = np.einsum("uv,xvc->xuc", mw, t)                        # site operator on s
+        P[w] = P[w] + t if w in P else t
+    return P
+
+
+def system_right(X3, R, W, pb):
+    """{w: P_w = E_w psi} for X3 = psi as (rows of the other part, 4, M_r), (s, r) the kept
+    part.  W: the MPO tensor of the kept site (channels w on the cut bond, b on the right
+    bond); pb: the parities of the right bond's channels."""
+    sgn = np.where(ops.SITE_N % 2 == 1, -1.0, 1.0)
+    P = {}
+    for (w, b), m in W.items():
+        mb = m * sgn[None, :] if pb[b] else m
+        t = np.einsum("uv,evr->eur", mb, X3) @ R[b].T              # (ne, 4, M_r')
+        P[w] = P[w] + t if w in P else t
+    return P
+
+
+def noise_left(X3, L, W, par_l, pa, pw):
+    """N = sum_w P_w P_w^T over rows (l, s), P_w from system_left."""
+    ml, _, nc = X3.shape
+    N = np.zeros((ml * 4, ml * 4))
+    for t in system_left(X3, L, W, par_l, pa, pw).values():
+        t2 = t.reshape(ml * 4, nc)
+        N += t2 @ t2.T
+    return N
+
+
+def noise_right(X3, R, W, pb):
+    """N = sum_w P_w^T P_w over rows (s, r), P_w from system_right."""
+    ne, _, mr = X3.shape
+    N = np.zeros((4 * mr, 4 * mr))
+    for t in system_right(X3, R, W, pb).values():
+        t2 = t.reshape(ne, 4 * mr)
+        N += t2.T @ t2
+    return N
+
+
+def _add_noise(X_rows, row_lab, allowed, N, noise):
+    """Density matrix rho = X X^T (+ noise * N / tr N on the allowed sectors' rows).  Rows of
+    a label outside `allowed` are zero in X and get no noise."""
+    rho = X_rows @ X_rows.T
+    if noise > 0 and N is not None:
+        ok = np.array([tuple(q) in allowed for q in row_lab])
+        Nm = N * ok[:, None] * ok[None, :]
+        tr = float(np.trace(Nm))
+        if tr > 0:
+            rho = rho + (noise / tr) * Nm
+    return rho
+
+
 # ---------------------------------------------------------------------------- truncation
 def _select(evals_by_sector, M, cutoff):
     """Keep the M largest eigenvalues over all sectors.  Eigenvalues <= cutoff * max are
@@ -306,26 +380,34 @@ def _select(evals_by_sector, M, cutoff):
     return kept
 
 
-def _sector_eigs(X, labels):
+def _sector_eigs(X, labels, rho=None):
     """Per sector q (sorted): eigenvalues (descending) and eigenvectors of X_q X_q^T,
-    X_q the rows of X labelled q."""
+    X_q the rows of X labelled q (or of the given rho's diagonal block q)."""
     secs = sorted({tuple(q) for q in labels})
     out = []
     for q in secs:
         rows = np.nonzero((labels[:, 0] == q[0]) & (labels[:, 1] == q[1]))[0]
-        xq = X[rows]
-        w, u = np.linalg.eigh(xq @ xq.T)
+        if rho is None:
+            xq = X[rows]
+            w, u = np.linalg.eigh(xq @ xq.T)
+        else:
+            w, u = np.linalg.eigh(rho[np.ix_(rows, rows)])
         out.append((q, rows, w[::-1], u[:, ::-1]))
     return out
 
 
-def left_split(psi, lab_l, M, cutoff=1e-14):
+def left_split(psi, lab_l, M, cutoff=1e-14, N=None, noise=0.0, lab_r=None):
     """psi (l s1, s2 r) -> A (l, s1, new) with A^T A = 1, C = A^T psi, new bond labels,
-    discarded weight."""
+    discarded weight (of the density matrix, noise included).  N, noise, lab_r: the
+    perturbative noise matrix over rows (l, s1), its weight and the right bond's labels."""
     ml, _, _, mr = psi.shape
     X = psi.reshape(ml * 4, 4 * mr)
     row_lab = (lab_l[:, None, :] + SITE_Q[None, :, :]).reshape(-1, 2)
-    eig = _sector_eigs(X, row_lab)
+    rho = None
+    if noise > 0:
+        allowed = {tuple(q) for q in (lab_r[None, :, :] - SITE_Q[:, None, :]).reshape(-1, 2)}
+        rho = _add_noise(X, row_lab, allowed, N, noise)
+    eig = _sector_eigs(X, row_lab, rho)
     kept = _select([e[2] for e in eig], M, cutoff)
     cols, lab = [], []
     for (q, rows, w, u), kq in zip(eig, kept):
@@ -341,13 +423,18 @@ def left_split(psi, lab_l, M, cutoff=1e-14):
     return A, C, np.array(lab, dtype=np.int64).reshape(-1, 2), total - keptw
 
 
-def right_split(psi, lab_r, M, cutoff=1e-14):
+def right_split(psi, lab_r, M, cutoff=1e-14, N=None, noise=0.0, lab_l=None):
     """psi (l s1, s2 r) -> B (new, s2, r) with B B^T = 1, C = psi B^T, new bond labels
-    (left-block quantum numbers of the new bond), discarded weight."""
+    (left-block quantum numbers of the new bond), discarded weight.  N: noise matrix over
+    rows (s2, r)."""
     ml, _, _, mr = psi.shape
     X = psi.reshape(ml * 4, 4 * mr)
     col_lab = (lab_r[None, :, :] - SITE_Q[:, None, :]).reshape(-1, 2)
-    eig = _sector_eigs(X.T, col_lab)
+    rho = None
+    if noise > 0:
+        allowed = {tuple(q) for q in (lab_l[:, None, :] + SITE_Q[None, :, :]).reshape(-1, 2)}
+        rho = _add_noise(X.T, col_lab, allowed, N, noise)
+    eig = _sector_eigs(X.T, col_lab, rho)
     kept = _select([e[2] for e in eig], M, cutoff)
     rows_out, lab = [], []
     for (q, cidx, w, u), kq in zip(eig, kept):
@@ -363,13 +450,16 @@ def right_split(psi, lab_r, M, cutoff=1e-14):
     return B, C, np.array(lab, dtype=np.int64).reshape(-1, 2), total - keptw
 
 
-def left_split1(psi, lab_l, M, cutoff=1e-14):
+def left_split1(psi, lab_l, M, cutoff=1e-14, N=None, noise=0.0, lab_r=None):
     """One-site psi (l s, r) -> A (l, s, new) with A^T A = 1, C = A^T psi (new, r), new
     bond labels, discarded weight (the density matrix of the left part, as left_split)."""
     ml, _, mr = psi.shape
     X = psi.reshape(ml * 4, mr)
     row_lab = (lab_l[:, None, :] + SITE_Q[None, :, :]).reshape(-1, 2)
-    eig = _sector_eigs(X, row_lab)
+    rho = None
+    if noise > 0:
+        rho = _add_noise(X, row_lab, {tuple(q) for q in lab_r}, N, noise)
+    eig = _sector_eigs(X, row_lab, rho)
     kept = _select([e[2] for e in eig], M, cutoff)
     cols, lab = [], []
     for (q, rows, w, u), kq in zip(eig, kept):
@@ -385,13 +475,16 @@ def left_split1(psi, lab_l, M, cutoff=1e-14):
             total - keptw)
 
 
-def right_split1(psi, lab_r, M, cutoff=1e-14):
+def right_split1(psi, lab_r, M, cutoff=1e-14, N=None, noise=0.0, lab_l=None):
     """One-site psi (l, s r) -> B (new, s, r) with B B^T = 1, C = psi B^T (l, new), new
     bond labels (left-block quantum numbers), discarded weight."""
     ml, _, mr = psi.shape
     X = psi.reshape(ml, 4 * mr)
     col_lab = (lab_r[None, :, :] - SITE_Q[:, None, :]).reshape(-1, 2)
-    eig = _sector_eigs(X.T, col_lab)
+    rho = None
+    if noise > 0:
+        rho = _add_noise(X.T, col_lab, {tuple(q) for q in lab_l}, N, noise)
+    eig = _sector_eigs(X.T, col_lab, rho)
     kept = _select([e[2] for e in eig], M, cutoff)
     rows_out, lab = [], []
     for (q, cidx, w, u), kq in zip(eig, kept):
@@ -443,8 +536,13 @@ class DMRG:
         self.stats.append({"window": i, "energy": e, "n_matvec": nmv, "resid2": rn2})
         return e
 
-    def move_right(self, i, M, cutoff):
-        A, C, lab, dw = left_split(self.psi, self.lab[i], M, cutoff)
+    def move_right(self, i, M, cutoff, noise=0.0):
+        N = None
+        if noise > 0:
+            m = self.mpo
+            N = noise_left(self.psi.reshape(self.psi.shape[0], 4, -1), self.L[i], m.W[i],
+                           parity_of(self.lab[i]), m.parity[i], m.parity[i + 1])
+        A, C, lab, dw = left_split(self.psi, self.lab[i], M, cutoff, N, noise, self.lab[i + 2])
         self.A[i] = A
         self.lab[i + 1] = lab
         self.L[i + 1] = left_env_update(self.L[i], A, self.mpo.W[i], self.lab[i],
@@ -452,8 +550,13 @@ class DMRG:
         self.psi = np.einsum("asb,btc->astc", C, self.A[i + 2])
         return dw
 
-    def move_left(self, i, M, cutoff):
-        B, C, lab, dw = right_split(self.psi, self.lab[i + 2], M, cutoff)
+    def move_left(self, i, M, cutoff, noise=0.0):
+        N = None
+        if noise > 0:
+            m = self.mpo
+            N = noise_right(self.psi.reshape(-1, 4, self.psi.shape[3]), self.R[i + 2], m.W[i + 1],
+                            m.parity[i + 2])
+        B, C, lab, dw = right_split(self.psi, self.lab[i + 2], M, cutoff, N, noise, self.lab[i])
         self.A[i + 1] = B
         self.lab[i + 1] = lab
         self.R[i + 1] = right_env_update(self.R[i + 2], B, self.mpo.W[i + 1],
@@ -461,30 +564,33 @@ class DMRG:
         self.psi = np.einsum("asb,btc->astc", self.A[i - 1], C)
         return dw
 
-    def sweep(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+    def sweep(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14, noise=0.0):
         n = self.n
         dws = []
         for i in range(0, n - 1):
             self.optimise(i, tol, max_iter, max_sub)
             if i < n - 2:
-                dws.append(self.move_right(i, M, cutoff))
+                dws.append(self.move_right(i, M, cutoff, noise))
         for i in range(n - 2, -1, -1):
             e = self.optimise(i, tol, max_iter, max_sub)
             if i > 0:
-                dws.append(self.move_left(i, M, cutoff))
+                dws.append(self.move_left(i, M, cutoff, noise))
         return e, max(dws) if dws else 0.0
 
-    def run(self, bond_dims, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14, dots=None):
+    def run(self, bond_dims, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14, dots=None,
+            noise=None):
         """Sweeps with bond dimension bond_dims[k]; dots[k] = 1 makes sweep k a one-site
         sweep (default: all two-site).  Mixing the two (Sec. 2.1.2) switches between the
-        two-site and the one-site wavefunction at the start of a sweep."""
+        two-site and the one-site wavefunction at the start of a sweep.  noise[k]: weight of
+        the perturbative noise in sweep k's splits (default none)."""
         energies = []
         for k, M in enumerate(bond_dims):
+            nz = 0.0 if noise is None else noise[k]
             if dots is not None and dots[k] == 1:
-                e, _ = self.sweep1(M, tol, max_iter, max_sub, cutoff)
+                e, _ = self.sweep1(M, tol, max_iter, max_sub, cutoff, nz)
             else:
                 self.to_two_site()
-                e, _ = self.sweep(M, tol, max_iter, max_sub, cutoff)
+                e, _ = self.sweep(M, tol, max_iter, max_sub, cutoff, nz)
             energies.append(e)
         return energies
 
@@ -523,8 +629,13 @@ class DMRG:
         self.stats.append({"window": i, "energy": e, "n_matvec": nmv, "resid2": rn2, "dot": 1})
         return e
 
-    def move_right1(self, i, M, cutoff):
-        A, C, lab, dw = left_split1(self.psi, self.lab[i], M, cutoff)
+    def move_right1(self, i, M, cutoff, noise=0.0):
+        N = None
+        if noise > 0:
+            m = self.mpo
+            N = noise_left(self.psi, self.L[i], m.W[i], parity_of(self.lab[i]), m.parity[i],
+                           m.parity[i + 1])
+        A, C, lab, dw = left_split1(self.psi, self.lab[i], M, cutoff, N, noise, self.lab[i + 1])
         self.A[i] = A
         self.lab[i + 1] = lab
         self.L[i + 1] = left_env_update(self.L[i], A, self.mpo.W[i], self.lab[i],
@@ -532,8 +643,12 @@ class DMRG:
         self.psi = np.einsum("ab,bsc->asc", C, self.A[i + 1])
         return dw
 
-    def move_left1(self, i, M, cutoff):
-        B, C, lab, dw = right_split1(self.psi, self.lab[i + 1], M, cutoff)
+    def move_left1(self, i, M, cutoff, noise=0.0):
+        N = None
+        if noise > 0:
+            m = self.mpo
+            N = noise_right(self.psi, self.R[i + 1], m.W[i], m.parity[i + 1])
+        B, C, lab, dw = right_split1(self.psi, self.lab[i + 1], M, cutoff, N, noise, self.lab[i])
         self.A[i] = B
         self.lab[i] = lab
         self.R[i] = right_env_update(self.R[i + 1], B, self.mpo.W[i], self.mpo.parity[i + 1],
@@ -541,20 +656,21 @@ class DMRG:
         self.psi = np.einsum("asb,bc->asc", self.A[i - 1], C)
         return dw
 
-    def sweep1(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14):
+    def sweep1(self, M, tol=1e-10, max_iter=30, max_sub=30, cutoff=1e-14, noise=0.0):
         """One-site sweep: forward over sites 0..n-1 (left split and move right after each
         site but the last), backward over sites n-1..0 (right split and move left after
         each site but site 0).  Without noise a split can keep at most the rank of psi's
-        matricisation, so bond dimensions never grow."""
+        matricisation, so bond dimensions never grow; the perturbative noise lets them grow
+        up to M."""
         n = self.n
         self.to_one_site(M, cutoff)
         dws = []
         for i in range(0, n):
             self.optimise1(i, tol, max_iter, max_sub)
             if i < n - 1:
-                dws.append(self.move_right1(i, M, cutoff))
+                dws.append(self.move_right1(i, M, cutoff, noise))
         for i in range(n - 1, -1, -1):
             e = self.optimise1(i, tol, max_iter, max_sub)
             if i > 0:
-                dws.append(self.move_left1(i, M, cutoff))
+                dws.append(self.move_left1(i, M, cutoff, noise))
         return e, max(dws) if dws else 0.0
