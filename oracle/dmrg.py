@@ -351,6 +351,88 @@ def _add_noise(X_rows, row_lab, allowed, N, noise):
     return rho
 
 
+def davidson_roots(matvec, diag, X0, tol=1e-10, max_iter=100, max_sub=40, allowed=None):
+    """The k lowest eigenpairs by the block form of the Davidson method (Davidson 1975 with
+    several roots, Liu 1978).
+
+    Guesses X0 (k arrays) are orthonormalised in order (twice Gram-Schmidt); one whose
+    remainder has norm <= 1e-8 is replaced by the unit vector at the smallest diagonal
+    element not used yet (ties by index) among the `allowed` entries (boolean mask of the
+    quantum-number-allowed elements; default all).  Subspace V (orthonormal), W = H V; Rayleigh-Ritz
+    on G = V^T W; the k lowest Ritz pairs (theta_j, u_j); r_j = W s_j - theta_j u_j.  Stop
+    when every |r_j|^2 <= tol or after max_iter products.  Otherwise the corrections
+    t_j = r_j / (D - theta_j) (denominators below 1e-8 in size set to 1e-8) of the roots with
+    |r_j|^2 > tol, in root order, are each orthogonalised twice against V (and the
+    corrections added before), normalised and added unless their norm is <= 1e-14.  When the
+    subspace cannot take them (size + count > max_sub) it restarts from the k Ritz vectors.
+    Returns (thetas, unit vectors, number of products, max |r_j|^2)."""
+    k = len(X0)
+    shape = X0[0].shape
+    d = diag.ravel()
+    V = []
+    used = set()
+    order = np.argsort(d, kind="stable")
+    if allowed is not None:
+        order = [j for j in order if allowed.ravel()[j]]
+    for x in X0:
+        v = x.ravel().astype(float).copy()
+        for _ in range(2):
+            for vv in V:
+                v = v - (vv @ v) * vv
+        nv = np.linalg.norm(v)
+        if nv <= 1e-8:
+            for idx in order:
+                if idx in used:
+                    continue
+                e = np.zeros(len(d))
+                e[idx] = 1.0
+                for _ in range(2):
+                    for vv in V:
+                        e = e - (vv @ e) * vv
+                if np.linalg.norm(e) > 1e-8:
+                    used.add(idx)
+                    v, nv = e, np.linalg.norm(e)
+                    break
+        V.append(v / nv)
+    Wl = [matvec(v.reshape(shape)).ravel() for v in V]
+    nmv = k
+    while True:
+        Vm, Wm = np.array(V).T, np.array(Wl).T
+        G = Vm.T @ Wm
+        G = 0.5 * (G + G.T)
+        evals, evecs = np.linalg.eigh(G)
+        thetas = evals[:k]
+        U, HU = Vm @ evecs[:, :k], Wm @ evecs[:, :k]
+        R = HU - U * thetas[None, :]
+        rn2 = np.sum(R * R, axis=0)
+        if np.all(rn2 <= tol) or nmv >= max_iter:
+            break
+        todo = [j for j in range(k) if rn2[j] > tol]
+        if len(V) + len(todo) > max_sub:
+            V = [U[:, j] / np.linalg.norm(U[:, j]) for j in range(k)]
+            Wl = [HU[:, j] / np.linalg.norm(U[:, j]) for j in range(k)]
+        added = 0
+        for j in todo:
+            den = d - thetas[j]
+            den = np.where(np.abs(den) < 1e-8, 1e-8, den)
+            t = R[:, j] / den
+            for _ in range(2):
+                for vv in V:
+                    t = t - (vv @ t) * vv
+            tn = np.linalg.norm(t)
+            if tn <= 1e-14:
+                continue
+            t = t / tn
+            V.append(t)
+            Wl.append(matvec(t.reshape(shape)).ravel())
+            nmv += 1
+            added += 1
+        if added == 0:
+            break
+    out = [(U[:, j] / np.linalg.norm(U[:, j])).reshape(shape) for j in range(k)]
+    return [float(x) for x in thetas], out, nmv, float(rn2.max())
+
+
 # ---------------------------------------------------------------------------- truncation
 def _select(evals_by_sector, M, cutoff):
     """Keep the M largest eigenvalues over all sectors.  Eigenvalues <= cutoff * max are
@@ -674,3 +756,86 @@ class DMRG:
             if i > 0:
                 dws.append(self.move_left1(i, M, cutoff, noise))
         return e, max(dws) if dws else 0.0
+
+
+class StateAveragedDMRG(DMRG):
+    """State-averaged two-site DMRG (Sec. 2.1.3 (i)): one set of site tensors for k states,
+    the centre carrying one wavefunction per state.  Each window solves for the k lowest
+    eigenpairs (davidson_roots) and splits with the averaged density matrix
+    rho = sum_j w_j psi_j psi_j^T (equal weights w_j = 1/k), every state then projected
+    onto the kept basis.  The average is an ordinary split of the k states stacked along the
+    discarded side, each scaled by sqrt(w_j): rows (l, s1) see X = [sqrt(w_j) X_j]_j.  The
+    states beyond the first start from the MPS's own psi completed by davidson_roots' rule.
+    Two-site sweeps only (the one-site schedule of the base class is not offered here)."""
+
+    def __init__(self, mpo, bonds, sites, n_roots, center=0):
+        super().__init__(mpo, bonds, sites, center)
+        self.k = n_roots
+        self.psis = [self.psi] + [np.zeros_like(self.psi) for _ in range(n_roots - 1)]
+
+    def optimise(self, i, tol, max_iter, max_sub):
+        h = self.heff(i)
+        ql = self.lab[i][:, None, None, None, :] + SITE_Q[None, :, None, None, :] + \
+            SITE_Q[None, None, :, None, :]
+        allowed = np.all(ql == self.lab[i + 2][None, None, None, :, :], axis=-1)
+        es, psis, nmv, rn2 = davidson_roots(h.apply, h.diag(), self.psis, tol, max_iter, max_sub,
+                                            allowed)
+        self.psis = psis
+        self.stats.append({"window": i, "energies": es, "energy": es[0], "n_matvec": nmv,
+                           "resid2": rn2})
+        return es
+
+    def sweep(self, M, tol=1e-10, max_iter=100, max_sub=40, cutoff=1e-14, noise=0.0):
+        n = self.n
+        dws = []
+        for i in range(0, n - 1):
+            es = self.optimise(i, tol, max_iter, max_sub)
+            if i < n - 2:
+                dws.append(self._split(i, M, cutoff, noise, forward=True))
+        for i in range(n - 2, -1, -1):
+            es = self.optimise(i, tol, max_iter, max_sub)
+            if i > 0:
+                dws.append(self._split(i, M, cutoff, noise, forward=False))
+        return es, max(dws) if dws else 0.0
+
+    def _split(self, i, M, cutoff, noise, forward):
+        """Averaged split of window i and the next guesses of every state."""
+        k, w = self.k, np.sqrt(1.0 / self.k)
+        ml, _, _, mr = self.psis[0].shape
+        m = self.mpo
+        if forward:
+            X = np.concatenate([w * p for p in self.psis], axis=3)        # (ml, 4, 4, k mr)
+            lab_stack = np.concatenate([self.lab[i + 2]] * k)
+            N = None
+            if noise > 0:
+                N = noise_left(X.reshape(ml, 4, -1), self.L[i], m.W[i], parity_of(self.lab[i]),
+                               m.parity[i], m.parity[i + 1])
+            A, C, lab, dw = left_split(X, self.lab[i], M, cutoff, N, noise, lab_stack)
+            self.A[i] = A
+            self.lab[i + 1] = lab
+            self.L[i + 1] = left_env_update(self.L[i], A, m.W[i], self.lab[i], len(m.chans[i + 1]))
+            self.psis = [np.einsum("asb,btc->astc", C[:, :, j * mr:(j + 1) * mr] / w, self.A[i + 2])
+                         for j in range(k)]
+        else:
+            X = np.concatenate([w * p for p in self.psis], axis=0)        # (k ml, 4, 4, mr)
+            lab_stack = np.concatenate([self.lab[i]] * k)
+            N = None
+            if noise > 0:
+                N = noise_right(X.reshape(-1, 4, mr), self.R[i + 2], m.W[i + 1], m.parity[i + 2])
+            B, C, lab, dw = right_split(X, self.lab[i + 2], M, cutoff, N, noise, lab_stack)
+            self.A[i + 1] = B
+            self.lab[i + 1] = lab
+            self.R[i + 1] = right_env_update(self.R[i + 2], B, m.W[i + 1], m.parity[i + 2],
+                                             len(m.chans[i + 1]))
+            self.psis = [np.einsum("asb,btc->astc", self.A[i - 1], C[j * ml:(j + 1) * ml] / w)
+                         for j in range(k)]
+        self.psi = self.psis[0]
+        return dw
+
+    def run(self, bond_dims, tol=1e-10, max_iter=100, max_sub=40, cutoff=1e-14, noise=None):
+        out = []
+        for k_, M in enumerate(bond_dims):
+            es, _ = self.sweep(M, tol, max_iter, max_sub, cutoff,
+                               0.0 if noise is None else noise[k_])
+            out.append(es)
+        return out
