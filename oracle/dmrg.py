@@ -433,6 +433,36 @@ def davidson_roots(matvec, diag, X0, tol=1e-10, max_iter=100, max_sub=40, allowe
     return [float(x) for x in thetas], out, nmv, float(rn2.max())
 
 
+def krylov_exp(matvec, x, t, tol=1e-12, max_k=40):
+    """exp(-t H) x by the Krylov (Lanczos) method: orthonormal basis V of span{x, Hx, ...}
+    (each new vector orthogonalised twice against all previous ones), T = V^T H V, and
+    y = |x| V exp(-t T) e_1.  With c = exp(-t (T - lambda_min)) e_1 (shifted against
+    overflow), it stops when the next vector's weight |beta_k| |c_k| is <= tol |c|, when the
+    space is exhausted (beta <= 1e-14 max(1, |lambda|)) or at max_k vectors."""
+    shape = x.shape
+    nx = np.linalg.norm(x)
+    V = [x.ravel() / nx]
+    HV = []
+    while True:
+        w = matvec(V[-1].reshape(shape)).ravel()
+        HV.append(w)
+        k = len(V)
+        T = np.array(V) @ np.array(HV).T
+        T = 0.5 * (T + T.T)
+        lam, U = np.linalg.eigh(T)
+        c = U @ (np.exp(-t * (lam - lam[0])) * U[0, :])      # exp(-t (T - lam_0)) e_1
+        for _ in range(2):
+            for v in V:
+                w = w - (v @ w) * v
+        beta = np.linalg.norm(w)
+        if beta * abs(c[-1]) <= tol * np.linalg.norm(c) \
+                or beta <= 1e-14 * max(1.0, np.abs(lam).max()) or k >= max_k:
+            break
+        V.append(w / beta)
+    y = nx * np.exp(-t * lam[0]) * (np.array(V).T @ c)
+    return y.reshape(shape)
+
+
 # ---------------------------------------------------------------------------- truncation
 def _select(evals_by_sector, M, cutoff):
     """Keep the M largest eigenvalues over all sectors.  Eigenvalues <= cutoff * max are
@@ -839,3 +869,51 @@ class StateAveragedDMRG(DMRG):
                                0.0 if noise is None else noise[k_])
             out.append(es)
         return out
+
+
+# ------------------------------------------------------------------------------------ TDVP
+def tdvp_step(d, tau, M, cutoff=1e-14, tol=1e-12, max_k=40):
+    """One second-order step of imaginary-time two-site TDVP (the projector-splitting
+    integrator, Haegeman et al. 2016; Sec. 2.7.3 lists TDVP among the paper's dynamics
+    methods, its H_eff product reused inside a Krylov exponential) on the two-site DMRG
+    state d (centre: the two-site psi of window (0, 1)): psi(tau) ~ exp(-tau H) psi(0).
+
+    Forward half (tau/2): for windows i = 0..n-2, psi <- exp(-tau/2 H2_i) psi; unless i is
+    the last window, split it (A_i left-orthonormal, truncated to M like a sweep split),
+    evolve the one-site remainder at site i+1 backwards, C <- exp(+tau/2 H1_{i+1}) C, and
+    contract it with A_{i+2} for the next window.  Backward half (tau/2): windows n-2..0
+    mirrored (B_{i+1}, C at site i evolved backwards, A_{i-1} . C).  Every local result is
+    normalised (imaginary time does not keep the norm; only the direction is wanted).
+    Returns the energy <psi|H|psi> at window 0 after the step and the largest discarded
+    weight."""
+    n = d.n
+    m = d.mpo
+    unit = lambda x: x / np.linalg.norm(x)
+    dws = []
+    for i in range(0, n - 1):
+        h = d.heff(i)
+        d.psi = unit(krylov_exp(h.apply, d.psi, 0.5 * tau, tol, max_k))
+        if i < n - 2:
+            A, C, lab, dw = left_split(d.psi, d.lab[i], M, cutoff)
+            dws.append(dw)
+            d.A[i] = A
+            d.lab[i + 1] = lab
+            d.L[i + 1] = left_env_update(d.L[i], A, m.W[i], d.lab[i], len(m.chans[i + 1]))
+            h1 = Heff1(m, i + 1, d.L[i + 1], d.R[i + 2], d.lab[i + 1])
+            C = unit(krylov_exp(h1.apply, C, -0.5 * tau, tol, max_k))
+            d.psi = np.einsum("asb,btc->astc", C, d.A[i + 2])
+    for i in range(n - 2, -1, -1):
+        h = d.heff(i)
+        d.psi = unit(krylov_exp(h.apply, d.psi, 0.5 * tau, tol, max_k))
+        if i > 0:
+            B, C, lab, dw = right_split(d.psi, d.lab[i + 2], M, cutoff)
+            dws.append(dw)
+            d.A[i + 1] = B
+            d.lab[i + 1] = lab
+            d.R[i + 1] = right_env_update(d.R[i + 2], B, m.W[i + 1], m.parity[i + 2],
+                                          len(m.chans[i + 1]))
+            h1 = Heff1(m, i, d.L[i], d.R[i + 1], d.lab[i])
+            C = unit(krylov_exp(h1.apply, C, -0.5 * tau, tol, max_k))
+            d.psi = np.einsum("asb,btc->astc", d.A[i - 1], C)
+    e = float(np.vdot(d.psi, d.heff(0).apply(d.psi)))
+    return e, max(dws) if dws else 0.0
