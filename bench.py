@@ -806,6 +806,31 @@ def main():
             mixed[name]["dE_vs_fp64"] = abs(mixed[name]["energy"] - mixed["fp64"]["energy"])
             mixed[name]["speedup_vs_fp64"] = mixed["fp64"]["sweep_ms"] / mixed[name]["sweep_ms"]
 
+    # sweep variants from the same state (one sweep each, FP64): the one-site sweep, a
+    # two-site sweep with perturbative noise and a three-root state-averaged sweep
+    variants = None
+    if args.prec == "fp64" and not args.no_mixed:
+        variants = {}
+        for name, kw in (("two_site", {}), ("one_site", {"dots": [1]}),
+                         ("two_site_noise_1e-5", {"noise": [1e-5]}),
+                         ("state_average_3roots", {"n_roots": 3, "dav_max_iter": 200,
+                                                   "max_subspace": 40})):
+            s3 = b2.b2_mps_import(ctx, bonds_now, sites_now, L, 0, center=0)
+            en3 = b2.b2_env_init(ctx, mpo_h, s3, center=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r3 = b2.b2_sweep(ctx, mpo_h, s3, en3, [M], **kw)[0]
+            torch.cuda.synchronize()
+            variants[name] = {"sweep_ms": (time.perf_counter() - t0) * 1e3,
+                              "energy": r3["energy"], "n_matvec": r3["n_matvec"],
+                              "max_bond": r3["max_bond"],
+                              "t_davidson_ms": r3["t_davidson"] * 1e3,
+                              "t_split_ms": r3["t_split"] * 1e3}
+            if "n_roots" in kw:
+                variants[name]["root_energy"] = r3["root_energy"]
+            b2.b2_free_env(en3)
+            b2.b2_free_mps(s3)
+
     if rank != 0:
         return
     peaks = measured_peaks(torch)
@@ -858,6 +883,8 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
     if mixed is not None:
         line["mixed_vs_fp64_sweep"] = mixed
+    if variants is not None:
+        line["sweep_variants"] = variants
     # the reference arm's sample on the GPU: FP64 products at the same window of the same
     # random MPS (like-for-like with the oracle's milliseconds per product)
     ms_p, fl_p = gpu_middle_window_product(b2, torch, ctx)

@@ -137,28 +137,37 @@ int b2_env_init(b2_ctx ctx, b2_mpo mpo, b2_mps mps, int center, b2_env* out);
  *   dir = -1: R_site from R_{site+1} and site tensor `site` (right-orthonormal) */
 int b2_env_update(b2_ctx ctx, b2_env env, int site, int dir);
 
-/* ------------------------------------------------------------ two-site effective H
- * Layout of the two-site wavefunction of window (site, site+1): number of FP64 elements
- * and of blocks.  The window's L_site and R_{site+2} must exist. */
+/* ------------------------------------------------------------------- effective H
+ * Windows.  The calls below that take `site` accept a window id: `site` itself names the
+ * two-site window (site, site+1) with environments L_site and R_{site+2}; site | B2_ONE_SITE
+ * names the one-site window of `site` (Sec. 2.1.2, one-site algorithm: the d = 4 space of
+ * one site) with environments L_site and R_{site+1}.  A one-site psi has the blocks
+ * (jl, s, 0, jr) on bonds (site, site+1), in the order and at the offsets of the MPS's site
+ * tensor `site`; its H_eff is sum over MPO channel pairs of L_a (x) W_site (x) R_b.
+ * Any other bit pattern, or a window past the chain's end, returns B2_EINVAL. */
+#define B2_ONE_SITE (1 << 24)
+/* Layout of the wavefunction of a window: number of FP64 elements and of blocks.  The
+ * window's environments must exist. */
 int b2_psi_layout(b2_ctx ctx, b2_env env, int site, int64_t* n_elem, int64_t* n_blocks);
 /* Block table of that layout: n_blocks x 6 int64 (jl, s1, s2, jr, offset, m_l*m_r). */
 int b2_psi_blocks(b2_ctx ctx, b2_env env, int site, int64_t* table);
-/* Two-site wavefunction of the MPS at window (site, site+1): the contraction of site
- * tensors site and site+1, written to psi (device, n_elem FP64). */
+/* Wavefunction of the MPS at a window: two sites, the contraction of site tensors site
+ * and site+1; one site, a copy of site tensor `site`.  Written to psi (device, n_elem
+ * FP64). */
 int b2_psi_from_mps(b2_ctx ctx, b2_env env, int site, double* psi);
-/* out = (H_eff - e_shift) psi for window (site, site+1) (Sec. 2.1.2; the operator is
- * sum over MPO channel pairs of L_a (x) W_site W_{site+1} (x) R_b).  psi, out: device,
+/* out = (H_eff - e_shift) psi for a window (Sec. 2.1.2; two sites: the operator is sum over
+ * MPO channel pairs of L_a (x) W_site W_{site+1} (x) R_b).  psi, out: device,
  * n_elem FP64 each, must not overlap.  algo_flops (host, may be NULL) receives the
  * algorithmic floating-point operations of the contraction (2 per multiply-add of the
  * block GEMMs actually performed).  Errors: B2_EINVAL on overlap or bad site. */
 int b2_heff_apply(b2_ctx ctx, b2_env env, int site, const double* psi, double* out,
                   b2_prec prec, double e_shift, double* algo_flops);
-/* Diagonal of H_eff for window (site, site+1) into diag (device, n_elem FP64): the
- * Davidson preconditioner. */
+/* Diagonal of H_eff for a window into diag (device, n_elem FP64): the Davidson
+ * preconditioner. */
 int b2_heff_diag(b2_ctx ctx, b2_env env, int site, double* diag);
 
 /* -------------------------------------------------------------------------- Davidson
- * Lowest eigenpair of H_eff of window (site, site+1) by the Davidson method (Sec. 2.1.3
+ * Lowest eigenpair of H_eff of a window (either width) by the Davidson method (Sec. 2.1.3
  * (iv)): Rayleigh-Ritz in FP64 on the GPU, residual r = H v - theta v, converged when
  * |r|^2 <= conv_tol; correction (D - theta)^-1 r with D the diagonal, orthogonalised
  * twice; a full subspace restarts from the Ritz vector.  With prec != B2_FP64 the
@@ -178,7 +187,7 @@ int b2_davidson(b2_ctx ctx, b2_env env, int site, double* psi, const b2_dav_opts
                 double* energy, int* n_matvec, double* resid2);
 
 /* ----------------------------------------------------------------------------- sweep
- * Two-site DMRG sweeps (Sec. 2.1.2).  One sweep = a forward half over windows 0..n-2
+ * DMRG sweeps (Sec. 2.1.2).  One two-site sweep = a forward half over windows 0..n-2
  * then a backward half over windows n-2..0.  After each window's Davidson the forward
  * half splits psi into a left-orthonormal site tensor by the density matrix of the left
  * part and moves right (except at window n-2); the backward half splits off a
@@ -188,7 +197,14 @@ int b2_davidson(b2_ctx ctx, b2_env env, int site, double* psi, const b2_dav_opts
  * the sector) using a batched FP64 Jacobi eigensolver on the GPU.  The next window's
  * guess is the split remainder contracted with the next site tensor.  The env must have
  * been made with center 0 for this mps, which must be in canonical form with centre 0;
- * on return the MPS is again centred at site 0 and the env consistent with it. */
+ * on return the MPS is again centred at site 0 and the env consistent with it.
+ * One-site sweeps (dots[k] = 1): forward over the one-site windows of sites 0..n-1,
+ * backward over n-1..0, with the same splits on one site (rows (l, s) forward, columns
+ * (s, r) backward); such a split keeps at most the rank of psi's matricisation, so bond
+ * dimensions do not grow.  Mixed schedules switch width at the start of a sweep: two ->
+ * one splits the window-0 psi backward with that sweep's M and cutoff; one -> two
+ * contracts the site-0 psi with site tensor 1. */
+#define B2_MAX_ROOTS 16
 typedef struct {
   int n_sweeps;
   const int* bond_dims;       /* host, n_sweeps entries: M of each sweep */
@@ -197,6 +213,27 @@ typedef struct {
   int max_subspace;
   b2_prec prec;
   double trunc_cutoff;        /* relative eigenvalue cutoff, e.g. 1e-14 */
+  const int* dots;            /* host, n_sweeps entries of 1 (one-site) or 2 (two-site), or
+                                 NULL: all two-site.  Other values: B2_EINVAL.  The batched
+                                 sweeps take two-site sweeps only (else B2_EUNSUPPORTED). */
+  int n_roots;                /* state-averaged roots (Sec. 2.1.3 (i)); 0 or 1: ground state.
+                                 k > 1 (at most B2_MAX_ROOTS): every window solves for the k
+                                 lowest eigenpairs (block Davidson, FP64 products; other
+                                 precisions or one-site sweeps: B2_EUNSUPPORTED) and splits
+                                 with the averaged density matrix sum_j psi_j psi_j^T / k;
+                                 each state is projected and carried to the next window.
+                                 Roots beyond the first start from the unit vectors at the
+                                 smallest H_eff diagonal elements.  The MPS left at the end
+                                 carries the first root at its centre. */
+  const double* noise;        /* host, n_sweeps entries >= 0, or NULL: weight of the
+                                 perturbative noise (Sec. 2.1.6; White 2005) in each sweep's
+                                 splits.  The MPO factorises exactly across the bond being
+                                 split, H = sum_w S_w (x) E_w; the kept part's density matrix
+                                 becomes rho + noise * N / tr N with N = sum_w P_w P_w^T,
+                                 P_w = S_w psi (forward) or E_w psi (backward), restricted to
+                                 the sectors the new bond can hold.  It lets one-site sweeps
+                                 grow the bond dimension.  Cost: one product per channel of
+                                 the cut bond.  Batched sweeps: B2_EUNSUPPORTED unless 0. */
 } b2_sweep_opts;
 typedef struct {
   double energy;              /* energy at the last window of the sweep */
@@ -208,9 +245,44 @@ typedef struct {
   int max_bond;               /* largest bond dimension after the sweep */
   double t_davidson;          /* wall time in the Davidson solves */
   double t_split;             /* wall time in truncation, environment update and guess */
+  double root_energy[B2_MAX_ROOTS];   /* energies of the n_roots states at the last window */
 } b2_sweep_result;
 int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts* opts,
              b2_sweep_result* per_sweep);
+
+/* ---------------------------------------------------------------------------- TDVP
+ * Imaginary-time evolution by the two-site time-dependent variational principle (Sec. 2.7.3:
+ * TDVP sweeps, and imaginary time needs only real arithmetic for a real Hamiltonian).  One
+ * step = the second-order projector-splitting integrator (Haegeman et al. 2016): a forward
+ * half over windows 0..n-2 and a backward half n-2..0, each window's two-site psi evolved by
+ * exp(-tau/2 H_eff), split (keeping at most bond_dim states, cutoff as in b2_sweep) and the
+ * one-site remainder evolved backwards by exp(+tau/2 H_eff) on its one-site window before it
+ * is contracted with the next site tensor.  Each exponential is a Krylov (Lanczos)
+ * approximation built from H_eff products (FP64; converged when the next Krylov vector's
+ * weight is <= krylov_tol of the result, at most krylov_max <= 64 vectors); every local
+ * result is normalised, so the MPS follows exp(-tau H) psi / |exp(-tau H) psi|.  With bond
+ * dimensions that keep every state the integrator is exact.  The env must have been made
+ * with center 0 for this mps (centred at site 0); on return the MPS is again centred at site
+ * 0.  Real-time evolution (complex arithmetic) is not offered.
+ * Errors: B2_EINVAL (bad options, n < 3, env not at centre 0), B2_ENOCONV (non-finite). */
+typedef struct {
+  int n_steps;
+  double tau;                 /* imaginary time per step, > 0 */
+  int bond_dim;               /* M of every split */
+  double trunc_cutoff;        /* relative eigenvalue cutoff (negative: 1e-14) */
+  double krylov_tol;          /* <= 0: 1e-12 */
+  int krylov_max;             /* <= 0: 40 */
+} b2_tdvp_opts;
+typedef struct {
+  double energy;              /* <psi|H|psi> of the normalised state after the step */
+  double discarded_weight;    /* largest of the step's splits */
+  double seconds;
+  double matvec_flops;        /* algorithmic flops of the step's H_eff products */
+  int n_matvec;
+  int max_bond;
+} b2_tdvp_result;
+int b2_tdvp(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_tdvp_opts* opts,
+            b2_tdvp_result* per_step);
 
 /* ------------------------------------------------------- many independent problems
  * Batched execution of independent problems on one context (one GPU, one stream): the

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libb2.so")
 B2_OK, B2_EINVAL, B2_ENOMEM, B2_ECUDA, B2_ENOCONV, B2_ETIMEOUT, B2_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 B2_FP64, B2_BF16X3, B2_TF32X3 = 0, 1, 2
 PRECISIONS = {"fp64": B2_FP64, "bf16x3": B2_BF16X3, "tf32x3": B2_TF32X3}
+B2_ONE_SITE = 1 << 24   # window id flag: site | B2_ONE_SITE is the one-site window of site
 _ERRNAMES = {-1: "B2_EINVAL", -2: "B2_ENOMEM", -3: "B2_ECUDA", -4: "B2_ENOCONV",
              -5: "B2_ETIMEOUT", -6: "B2_EUNSUPPORTED"}
 
@@ -35,13 +36,24 @@ class DavOpts(ctypes.Structure):
 
 class SweepOpts(ctypes.Structure):
     _fields_ = [("n_sweeps", _i), ("bond_dims", ctypes.POINTER(_i)), ("conv_tol", _d),
-                ("dav_max_iter", _i), ("max_subspace", _i), ("prec", _i), ("trunc_cutoff", _d)]
+                ("dav_max_iter", _i), ("max_subspace", _i), ("prec", _i), ("trunc_cutoff", _d),
+                ("dots", ctypes.POINTER(_i)), ("n_roots", _i), ("noise", ctypes.POINTER(_d))]
+
+
+class TdvpOpts(ctypes.Structure):
+    _fields_ = [("n_steps", _i), ("tau", _d), ("bond_dim", _i), ("trunc_cutoff", _d),
+                ("krylov_tol", _d), ("krylov_max", _i)]
+
+
+class TdvpResult(ctypes.Structure):
+    _fields_ = [("energy", _d), ("discarded_weight", _d), ("seconds", _d), ("matvec_flops", _d),
+                ("n_matvec", _i), ("max_bond", _i)]
 
 
 class SweepResult(ctypes.Structure):
     _fields_ = [("energy", _d), ("discarded_weight", _d), ("seconds", _d), ("matvec_flops", _d),
                 ("other_flops", _d), ("n_matvec", _i), ("max_bond", _i), ("t_davidson", _d),
-                ("t_split", _d)]
+                ("t_split", _d), ("root_energy", _d * 16)]
 
 
 class ProfileData(ctypes.Structure):
@@ -70,6 +82,7 @@ _sig = {
     "b2_davidson": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(DavOpts), ctypes.POINTER(_d),
                          ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "b2_sweep": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepResult)]),
+    "b2_tdvp": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(TdvpOpts), ctypes.POINTER(TdvpResult)]),
     "b2_eigh_batched": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "b2_eigh_batched_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "b2_rdm_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -278,12 +291,33 @@ def b2_davidson(ctx, env, site, psi, max_iter=30, max_subspace=30, conv_tol=1e-1
 
 
 def b2_sweep(ctx, mpo, mps, env, bond_dims, conv_tol=1e-10, dav_max_iter=30, max_subspace=30,
-             prec=B2_FP64, trunc_cutoff=1e-14):
+             prec=B2_FP64, trunc_cutoff=1e-14, dots=None, noise=None, n_roots=1):
+    """dots: None (all two-site) or one entry of 1 / 2 per sweep; noise: None or one
+    perturbative-noise weight per sweep; n_roots: state-averaged roots (result key
+    "root_energy": their energies)."""
     bd = (_i * len(bond_dims))(*bond_dims)
-    o = SweepOpts(len(bond_dims), bd, conv_tol, dav_max_iter, max_subspace, prec, trunc_cutoff)
+    dt = None if dots is None else (_i * len(dots))(*dots)
+    nz = None if noise is None else (_d * len(noise))(*noise)
+    o = SweepOpts(len(bond_dims), bd, conv_tol, dav_max_iter, max_subspace, prec, trunc_cutoff,
+                  dt, n_roots, nz)
     res = (SweepResult * len(bond_dims))()
     _check(ctx.h, lib.b2_sweep(ctx.h, mpo, mps, env, ctypes.byref(o), res))
-    return [{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res]
+    return [_result(r, n_roots) for r in res]
+
+
+def b2_tdvp(ctx, mpo, mps, env, n_steps, tau, bond_dim, trunc_cutoff=1e-14, krylov_tol=1e-12,
+            krylov_max=40):
+    """Imaginary-time two-site TDVP steps; returns one dict per step."""
+    o = TdvpOpts(n_steps, tau, bond_dim, trunc_cutoff, krylov_tol, krylov_max)
+    res = (TdvpResult * max(1, n_steps))()
+    _check(ctx.h, lib.b2_tdvp(ctx.h, mpo, mps, env, ctypes.byref(o), res))
+    return [{f: getattr(r, f) for f, _ in TdvpResult._fields_} for r in res[:n_steps]]
+
+
+def _result(r, n_roots=1):
+    d = {f: getattr(r, f) for f, _ in SweepResult._fields_ if f != "root_energy"}
+    d["root_energy"] = [r.root_energy[j] for j in range(max(1, n_roots))]
+    return d
 
 
 def b2_eigh_batched(ctx, dims, a, evals, evecs):
@@ -338,7 +372,7 @@ def b2_sweep_batched(ctx, envs, bond_dims, conv_tol=1e-10, dav_max_iter=30, max_
     res = (SweepResult * (n * len(bond_dims)))()
     _check(ctx.h, lib.b2_sweep_batched(ctx.h, n, _handles(envs), ctypes.byref(o), res))
     k = len(bond_dims)
-    return [[{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res[p * k:(p + 1) * k]]
+    return [[_result(r) for r in res[p * k:(p + 1) * k]]
             for p in range(n)]
 
 
@@ -353,7 +387,7 @@ def b2_sweep_batched_dims(ctx, envs, bond_dims, conv_tol=1e-10, dav_max_iter=30,
     res = (SweepResult * (n * k))()
     _check(ctx.h, lib.b2_sweep_batched_dims(ctx.h, n, _handles(envs), ctypes.byref(o),
                                             flat.ctypes.data, res))
-    return [[{f: getattr(r, f) for f, _ in SweepResult._fields_} for r in res[p * k:(p + 1) * k]]
+    return [[_result(r) for r in res[p * k:(p + 1) * k]]
             for p in range(n)]
 
 

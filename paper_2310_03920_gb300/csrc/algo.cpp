@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <unordered_map>
 
 #include "algo.hpp"
 
@@ -249,6 +251,169 @@ static DavidsonResult davidson_core(b2_env_s* env, int site, double* psi, const 
   res.n_matvec = nmv;
   sync(c);
   return res;
+}
+
+// Lowest n_roots eigenpairs of H_eff (FP64 products): the block form of the Davidson method
+// (several roots, Liu 1978).  psis: n_roots vectors of the window layout, one after the
+// other; in: guesses, out: unit eigenvectors.  Guesses are orthonormalised in order (two
+// Gram-Schmidt passes); one whose remainder has norm <= 1e-8 is replaced by the unit vector at
+// the smallest diagonal element not used yet (ties by position).  Rayleigh-Ritz on V^T H V;
+// the n_roots lowest Ritz pairs; stop when every |r_j|^2 <= conv_tol or after max_iter
+// products; else the corrections r_j / (D - theta_j) of the unconverged roots, in root order,
+// are orthogonalised twice against the subspace and added unless their norm is <= 1e-14; a
+// subspace that cannot take them restarts from the Ritz vectors.  One host synchronisation
+// per iteration and per added vector (its norm decides whether it is kept).
+std::vector<double> davidson_roots(b2_env_s* env, int win, double* psis, int n_roots,
+                                   const b2_dav_opts& o, int* n_matvec, double* max_resid2,
+                                   double* flops_out) {
+  Ctx* c = env->ctx;
+  WindowProgram& wp = window_program(env, win);
+  const int64_t n = wp.psi.size;
+  const int k = n_roots;
+  B2_REQUIRE(n > 0, B2_EINVAL, "empty wavefunction");
+  B2_REQUIRE(k >= 1 && k <= 16 && int64_t(k) <= n, B2_EINVAL, "n_roots must be in [1, 16] and <= size");
+  const int kmax = std::max(2 * k, std::min(o.max_subspace > 0 ? o.max_subspace : 40, 64));
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 100;
+  const double tol = o.conv_tol > 0 ? o.conv_tol : 1e-10;
+  DevBuf V(c, sizeof(double) * n * kmax), W(c, sizeof(double) * n * kmax);
+  DevBuf diag(c, sizeof(double) * n), U(c, sizeof(double) * n * k), HU(c, sizeof(double) * n * k),
+      T(c, sizeof(double) * n * k), tmp(c, sizeof(double) * n);
+  const int kPart = 256 * 16;
+  DevBuf small(c, sizeof(double) * (kPart + 4 * kmax * kmax + 8 * kmax + 4 * 16 + 16));
+  double* part = small.as<double>();
+  double* VW = part + kPart;
+  double* G = VW + kmax * kmax;
+  double* evecs = G + kmax * kmax;
+  double* evals = evecs + kmax * kmax;
+  double* cvec = evals + kmax;
+  double* r2d = cvec + 2 * kmax;     // |r_j|^2
+  double* nrm = r2d + 16;            // norms^2 of vectors being added
+  double* Vp = V.as<double>();
+  double* Wp = W.as<double>();
+  double fl = 0, flops = 0;
+  int nmv = 0, m = 0;
+  heff_diag(env, win, diag.as<double>());
+  auto orthonormal_add = [&](const double* x, double thresh2) -> bool {
+    // x -> V[m] after two passes against V[0..m); kept if |remainder|^2 > thresh2
+    double* vm = Vp + int64_t(m) * n;
+    B2_CUDA(cudaMemcpyAsync(vm, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {
+      b2k::launch_multidot(m, Vp, n, vm, n, part, cvec, 1, c->stream);
+      b2k::launch_multiaxpy(m, Vp, n, cvec, vm, n, -1.0, c->stream);
+    }
+    b2k::launch_multidot(1, vm, n, vm, n, part, nrm, 1, c->stream);
+    double h2 = 0;
+    B2_CUDA(cudaMemcpyAsync(&h2, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    if (!(h2 > thresh2)) return false;
+    b2k::launch_scale_inv_sqrt(vm, n, nrm, c->stream);
+    return true;
+  };
+  auto add_product = [&]() {   // W[m] = H V[m]; VW updated; m += 1
+    double* vm = Vp + int64_t(m) * n;
+    double* wm = Wp + int64_t(m) * n;
+    heff_apply(env, win, vm, wm, 0.0, &fl, B2_FP64);
+    flops += fl;
+    ++nmv;
+    b2k::launch_multidot(m + 1, Vp, n, wm, n, part, VW + m, kmax, c->stream);
+    if (m > 0) b2k::launch_multidot(m, Wp, n, vm, n, part, VW + int64_t(m) * kmax, 1, c->stream);
+    ++m;
+  };
+  // guesses, completed by unit vectors at the smallest unused diagonal elements
+  std::vector<int64_t> order;
+  size_t next_unit = 0;
+  for (int j = 0; j < k; ++j) {
+    if (orthonormal_add(psis + int64_t(j) * n, 1e-16)) {
+      add_product();
+      continue;
+    }
+    if (order.empty()) {
+      std::vector<double> dh(n);
+      B2_CUDA(cudaMemcpyAsync(dh.data(), diag.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+      sync(c);
+      order.resize(n);
+      for (int64_t x = 0; x < n; ++x) order[x] = x;
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return dh[a] < dh[b]; });
+    }
+    bool ok = false;
+    while (!ok && next_unit < order.size()) {
+      B2_CUDA(cudaMemsetAsync(tmp.ptr, 0, sizeof(double) * n, c->stream));
+      const double one = 1.0;
+      B2_CUDA(cudaMemcpyAsync(tmp.as<double>() + order[next_unit++], &one, sizeof(double),
+                              cudaMemcpyHostToDevice, c->stream));
+      ok = orthonormal_add(tmp.as<double>(), 1e-16);
+    }
+    B2_REQUIRE(ok, B2_ENOCONV, "no independent start vector");
+    add_product();
+  }
+  // dims table 0..kmax on the device for the small eigensolver
+  std::vector<int> dims_h(kmax + 1);
+  for (int x = 0; x <= kmax; ++x) dims_h[x] = x;
+  int64_t offs_h[2] = {0, 0};
+  DevBuf d_dims, d_offs(c, sizeof(int64_t) * 2);
+  upload(c, d_dims, dims_h);
+  B2_CUDA(cudaMemcpyAsync(d_offs.ptr, offs_h, sizeof(offs_h), cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> theta(k), r2(k);
+  for (;;) {
+    b2k::launch_symmetrize(m, VW, kmax, G, c->stream);
+    b2k::launch_jacobi(1, d_dims.as<int>() + m, d_offs.as<int64_t>(), d_offs.as<int64_t>(), G,
+                       evals, evecs, nullptr, d_offs.as<int64_t>(), m, c->stream);
+    for (int j = 0; j < k; ++j)   // root j: eigenvalue m-1-j of the descending list
+      b2k::launch_ritz(m, Vp, Wp, n, evecs + (m - 1 - j), m, evals + (m - 1 - j), diag.as<double>(),
+                       U.as<double>() + int64_t(j) * n, HU.as<double>() + int64_t(j) * n,
+                       T.as<double>() + int64_t(j) * n, n, part, r2d + j, c->stream);
+    B2_CUDA(cudaMemcpyAsync(r2.data(), r2d, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    for (int j = 0; j < k; ++j)
+      B2_CUDA(cudaMemcpyAsync(&theta[j], evals + (m - 1 - j), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+    sync(c);
+    for (int j = 0; j < k; ++j)
+      B2_REQUIRE(std::isfinite(r2[j]) && std::isfinite(theta[j]), B2_ENOCONV,
+                 "Davidson produced a non-finite value");
+    std::vector<int> todo;
+    for (int j = 0; j < k; ++j)
+      if (r2[j] > tol) todo.push_back(j);
+    if (std::getenv("B2_TRACE_DAVIDSON")) {
+      std::fprintf(stderr, "roots win %d m %d nmv %d", win, m, nmv);
+      for (int j = 0; j < k; ++j) std::fprintf(stderr, " (%.12f %.2e)", theta[j], r2[j]);
+      std::fprintf(stderr, "\n");
+    }
+    if (todo.empty() || nmv >= max_iter) break;
+    if (m + int(todo.size()) > kmax) {   // restart from the Ritz vectors
+      for (int j = 0; j < k; ++j) {
+        double* uj = U.as<double>() + int64_t(j) * n;
+        b2k::launch_multidot(1, uj, n, uj, n, part, nrm, 1, c->stream);
+        B2_CUDA(cudaMemcpyAsync(Vp + int64_t(j) * n, uj, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        B2_CUDA(cudaMemcpyAsync(Wp + int64_t(j) * n, HU.as<double>() + int64_t(j) * n,
+                                sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        b2k::launch_scale_inv_sqrt(Vp + int64_t(j) * n, n, nrm, c->stream);
+        b2k::launch_scale_inv_sqrt(Wp + int64_t(j) * n, n, nrm, c->stream);
+      }
+      m = k;
+      for (int j = 0; j < k; ++j)
+        b2k::launch_multidot(k, Vp, n, Wp + int64_t(j) * n, n, part, VW + j, kmax, c->stream);
+    }
+    int added = 0;
+    for (int j : todo) {
+      if (!orthonormal_add(T.as<double>() + int64_t(j) * n, 1e-28)) continue;
+      add_product();
+      ++added;
+    }
+    if (added == 0) break;
+  }
+  double mx = 0;
+  for (int j = 0; j < k; ++j) {
+    double* uj = U.as<double>() + int64_t(j) * n;
+    b2k::launch_multidot(1, uj, n, uj, n, part, nrm, 1, c->stream);
+    B2_CUDA(cudaMemcpyAsync(psis + int64_t(j) * n, uj, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    b2k::launch_scale_inv_sqrt(psis + int64_t(j) * n, n, nrm, c->stream);
+    mx = std::max(mx, r2[j]);
+  }
+  sync(c);
+  if (n_matvec) *n_matvec = nmv;
+  if (max_resid2) *max_resid2 = mx;
+  if (flops_out) *flops_out = flops;
+  return theta;
 }
 
 // Davidson for H_eff.  FP64: the textbook iteration.  Split precision (mixed-precision
@@ -500,16 +665,48 @@ static std::vector<int> eig_and_select(Ctx* c, std::vector<RhoSector>& secs, Dev
   return kept;
 }
 
-// Forward split of window i: psi -> A_i (left-orthonormal, new bond i+1) and the guess for
-// window i+1.  Updates mps->bonds[i+1], mps->sites[i], L_{i+1}; writes the new psi.
-void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
-                double* flops) {
+// ------------------------------------------------------------- perturbative noise
+// The MPO factorises exactly across the bond being split, H = sum_w S_w (x) E_w (channels w
+// of that bond; S_w = sum_a (-1)^{p(a) N(l)} L_a (x) W[a, w] diag((-1)^{p(w) n(s)}) on the
+// left part, E_w = sum_b W[w, b] diag((-1)^{p(b) n(s)}) (x) R_b on the right part).  The
+// perturbative noise (White 2005) adds to the kept part's density matrix the weight that the
+// kept part's operators move psi into: N = sum_w P_w P_w^T, P_w = S_w psi (forward split) or
+// E_w psi (backward split), normalised so that it adds total weight `noise`:
+// rho' = rho + noise * N / tr N.  Sign factors on the other part's indices cancel in N and
+// are left out.  Rows of sectors the new bond cannot hold get no noise.  The products P_w
+// are blocks of their own (one per (w, row block, column block)); tr N = |P|^2.
+struct NoiseBlock {
+  int w, row, col;      // channel, row part index, column part index (meaning per direction)
+  int64_t off;
+  int m_row, m_col;
+};
+
+static double norm2_device(Ctx* c, const double* x, int64_t n) {
+  if (n <= 0) return 0.0;
+  DevBuf sc(c, sizeof(double) * (256 * 16 + 1));
+  double* part = sc.as<double>();
+  b2k::launch_multidot(1, x, n, x, n, part, part + 256 * 16, 1, c->stream);
+  double v = 0;
+  B2_CUDA(cudaMemcpyAsync(&v, part + 256 * 16, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  sync(c);
+  return v;
+}
+
+// Forward split of window win (site i): psi -> A_i (left-orthonormal, new bond i+1) and the
+// guess for the next window of the same width.  Updates mps->bonds[i+1], mps->sites[i],
+// L_{i+1}; writes the new psi.  Rows of the density matrix are (jl, s1) in both widths; a
+// one-site psi has only s2 = 0, so its columns are the right bond alone.
+void split_left(b2_env_s* env, int win, DevBuf& psi, int M, double cutoff, double* discarded,
+                double* flops, double noise, int nroot, bool keep_centre) {
   Ctx* c = env->ctx;
+  const int i = win_site(win), ns = win_nsite(win);
   Tracer tr(c, "split_left", i);
   b2_mps_s* mps = env->mps;
-  WindowProgram& wp = window_program(env, i);
+  WindowProgram& wp = window_program(env, win);
   const PsiLayout lay = wp.psi;
-  const Bond& bl = mps->bonds[i];
+  const int64_t n = lay.size;               // psi holds nroot states of this layout
+  const double wr = 1.0 / nroot;            // state-average weight
+  const Bond bl = mps->bonds[i];
   // sectors of bond i+1 from (jl, s1)
   std::map<int64_t, int> sidx;
   std::vector<RhoSector> secs;
@@ -549,36 +746,140 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   DevBuf evecs(c, sizeof(double) * std::max<int64_t>(tot, 1));
   // rho_q[(jl,s1),(jl',s1')] = sum_s2 psi(jl,s1,s2) psi(jl',s1',s2)^T
   GemmProgram prog;
-  for (auto& r : secs)
-    for (size_t a = 0; a < r.parts.size(); ++a)
-      for (size_t b = 0; b < r.parts.size(); ++b) {
+  std::vector<std::vector<int>> out_of(secs.size());
+  std::vector<std::pair<int, int>> part_of(size_t(bl.size()) * 4, {-1, -1});   // (sector, part)
+  for (size_t j = 0; j < secs.size(); ++j)
+    for (size_t a = 0; a < secs[j].parts.size(); ++a)
+      part_of[size_t(secs[j].parts[a].first) * 4 + secs[j].parts[a].second] = {int(j), int(a)};
+  for (size_t j = 0; j < secs.size(); ++j)
+    for (size_t a = 0; a < secs[j].parts.size(); ++a)
+      for (size_t b = 0; b < secs[j].parts.size(); ++b) {
+        const RhoSector& r = secs[j];
         int ja = r.parts[a].first, sa = r.parts[a].second;
         int jb = r.parts[b].first, sb = r.parts[b].second;
         int o = prog.add_out(1, r.off + int64_t(r.part_off[a]) * r.dim + r.part_off[b], bl.m[ja],
                              bl.m[jb], r.dim, false);
+        out_of[j].push_back(o);
         for (int s2 = 0; s2 < 4; ++s2) {
           int pa = lay.find(ja, sa, s2), pb = lay.find(jb, sb, s2);
           if (pa < 0 || pb < 0) continue;
           const PsiBlock& A = lay.blocks[pa];
           const PsiBlock& B = lay.blocks[pb];
-          GemmTerm t{};
-          t.offP = A.off; t.bufP = 0; t.ldP = A.mr;
-          t.offX = B.off; t.bufX = 0; t.ldX = B.mr;     // op(X) = B^T
-          t.K1 = A.mr;
-          t.flags = kTwoOp | kTransQ;
-          t.alpha = 1.0;
-          prog.add_term(o, t);
+          for (int rt = 0; rt < nroot; ++rt) {
+            GemmTerm t{};
+            t.offP = A.off + rt * n; t.bufP = 0; t.ldP = A.mr;
+            t.offX = B.off + rt * n; t.bufX = 0; t.ldX = B.mr;     // op(X) = B^T
+            t.K1 = A.mr;
+            t.flags = kTwoOp | kTransQ;
+            t.alpha = wr;
+            prog.add_term(o, t);
+          }
         }
       }
+  // noise: P_w(jl', s1'; s2, jr) = sum_{a, s1} c (-1)^{p(a) N(jl)} L_a(jl' <- jl) psi(jl, s1, s2, jr)
+  DevBuf pbuf;
+  if (noise > 0) {
+    const EnvBond& L = env->L[i];
+    b2_mpo_s* mpo = env->mpo;
+    std::vector<NoiseBlock> nb_;
+    std::vector<std::pair<int, GemmTerm>> pterms;   // (block, term) of one state
+    std::unordered_map<int64_t, int> nidx;
+    const int64_t ncol = int64_t(4) * mps->bonds[i + ns].size();
+    GemmProgram pp;
+    int64_t psize = 0;                              // per state
+    for (const auto& e : mpo->W[i]) {
+      const int a = e.w, w = e.w2;
+      const bool pw = mpo->parity[i + 1][w] != 0, pa = mpo->parity[i][a] != 0;
+      for (int u = 0; u < 16; ++u) {
+        if (e.m[u] == 0) continue;
+        const int s1p = u / 4, s1 = u % 4;
+        const double sg = (pw && (kSiteN[s1] & 1)) ? -1.0 : 1.0;
+        for (int jl = 0; jl < bl.size(); ++jl) {
+          const int lb = L.find(a, jl);
+          if (lb < 0) continue;
+          const int jlp = L.blocks[lb].jb;
+          const int row = jlp * 4 + s1p;
+          if (part_of[row].first < 0) continue;
+          for (int s2 = 0; s2 < 4; ++s2) {
+            const int ib = lay.find(jl, s1, s2);
+            if (ib < 0) continue;
+            const PsiBlock& P = lay.blocks[ib];
+            const int col = P.jr * 4 + s2;
+            const int64_t key = (int64_t(w) * bl.size() * 4 + row) * ncol + col;
+            auto it = nidx.find(key);
+            int o;
+            if (it == nidx.end()) {
+              o = int(nb_.size());
+              nidx.emplace(key, o);
+              nb_.push_back({w, row, col, psize, bl.m[jlp], P.mr});
+              psize += int64_t(bl.m[jlp]) * P.mr;
+            } else {
+              o = it->second;
+            }
+            GemmTerm t{};
+            t.offP = L.blocks[lb].off; t.bufP = 2; t.ldP = P.ml;   // L_a [m_jl' x m_jl]
+            t.offX = P.off; t.bufX = 0; t.ldX = P.mr;               // psi [m_jl x m_jr]
+            t.K1 = P.ml;
+            t.flags = kTwoOp;
+            t.alpha = e.m[u] * sg * ((pa && (bl.q[jl].n & 1)) ? -1.0 : 1.0);
+            pterms.push_back({o, t});
+          }
+        }
+      }
+    }
+    if (psize > 0) {
+      // the states' products side by side, each scaled by sqrt(w): N = sum_j w_j N_j
+      const double sw = std::sqrt(wr);
+      for (int rt = 0; rt < nroot; ++rt)
+        for (const auto& b : nb_) pp.add_out(1, rt * psize + b.off, b.m_row, b.m_col, b.m_col, false);
+      for (int rt = 0; rt < nroot; ++rt)
+        for (auto bt : pterms) {
+          bt.second.offX += rt * n;
+          bt.second.alpha *= sw;
+          pp.add_term(rt * int(nb_.size()) + bt.first, bt.second);
+        }
+      pp.finalize(c);
+      pbuf.reset(c, sizeof(double) * size_t(psize) * nroot);
+      BufTable pt{};
+      pt.p[0] = psi.as<double>();
+      pt.p[1] = pbuf.as<double>();
+      pt.p[2] = L.data.as<double>();
+      pp.launch(c, pt);
+      *flops += pp.flops;
+      const double trN = norm2_device(c, pbuf.as<double>(), psize * nroot);
+      if (trN > 0) {
+        // Gram terms per environment column: rho[(row x), (row y)] += scale P_x P_y^T
+        std::map<int64_t, std::vector<int>> by_col;   // key: w * ncol + col
+        for (size_t x = 0; x < nb_.size(); ++x) by_col[nb_[x].w * ncol + nb_[x].col].push_back(int(x));
+        for (auto& kv : by_col)
+          for (int x : kv.second)
+            for (int y : kv.second) {
+              const auto px = part_of[nb_[x].row], py = part_of[nb_[y].row];
+              if (px.first != py.first) continue;
+              const int np_ = int(secs[px.first].parts.size());
+              for (int rt = 0; rt < nroot; ++rt) {
+                GemmTerm t{};
+                t.offP = rt * psize + nb_[x].off; t.bufP = 2; t.ldP = nb_[x].m_col;
+                t.offX = rt * psize + nb_[y].off; t.bufX = 2; t.ldX = nb_[y].m_col;   // P_y^T
+                t.K1 = nb_[x].m_col;
+                t.flags = kTwoOp | kTransQ;
+                t.alpha = noise / trN;
+                prog.add_term(out_of[px.first][size_t(px.second) * np_ + py.second], t);
+              }
+            }
+      }
+    }
+  }
   prog.finalize(c);
   BufTable bt{};
   bt.p[0] = psi.as<double>();
   bt.p[1] = rho.as<double>();
+  bt.p[2] = pbuf.as<double>();
   prog.launch(c, bt);
   *flops += prog.flops;
   tr.mark("rho");
   std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded,
-                                         &env->rho_cache[2 * i]);
+                                         &env->rho_cache[4 * i + 2 * (ns == 1)]);
   tr.mark("eig+select");
 
   // new bond i+1 and A_i
@@ -624,14 +925,16 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   b2k::launch_copy(int(copies.size()), d_copies.as<b2k::CopyTask>(), cb, c->stream);
   B2_CUDA(cudaGetLastError());
 
-  // C(jt, s2 -> jr) = sum_{(jl,s1) in jt} A(jl,s1,jt)^T psi(jl,s1,s2)
-  const Bond& br = mps->bonds[i + 2];
+  // C(jt, s2 -> jr) = sum_{(jl,s1) in jt} A(jl,s1,jt)^T psi(jl,s1,s2)  (one-site: s2 = 0,
+  // C is the matrix from the new bond i+1 to the old one; its blocks s2 > 0 stay unused)
+  const Bond br = mps->bonds[i + ns];
   SiteTensor C;
   C.build(nb, br);
-  C.data.reset(c, sizeof(double) * std::max<int64_t>(C.size, 1));
+  C.data.reset(c, sizeof(double) * std::max<int64_t>(C.size * nroot, 1));   // one C per state
   GemmProgram pc;
+  for (int rt = 0; rt < nroot; ++rt)
   for (const auto& cbk : C.blocks) {
-    int o = pc.add_out(1, cbk.off, cbk.ml, cbk.mr, cbk.mr, false);
+    int o = pc.add_out(1, rt * C.size + cbk.off, cbk.ml, cbk.mr, cbk.mr, false);
     int j = -1;
     for (size_t x = 0; x < secs.size(); ++x)
       if (new_idx[x] == cbk.jl) j = int(x);
@@ -645,7 +948,7 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
       const SiteBlock& Ab = A.blocks[A.find(jl, s1)];
       GemmTerm t{};
       t.offP = Ab.off; t.bufP = 2; t.ldP = Ab.mr;    // op(P) = A^T [m_jt x m_jl]
-      t.offX = P.off; t.bufX = 0; t.ldX = P.mr;
+      t.offX = P.off + rt * n; t.bufX = 0; t.ldX = P.mr;
       t.K1 = Ab.ml;
       t.flags = kTwoOp | kTransP;
       t.alpha = 1.0;
@@ -660,37 +963,57 @@ void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double*
   pc.launch(c, bc);
   *flops += pc.flops;
 
-  // commit: site i, bond i+1; environments on bond i+1 change
+  // commit: site i, bond i+1; environments on bond i+1 change.  br_mid: the bond between
+  // C and the next site tensor (bond i+2 for two sites, the old bond i+1 for one)
+  const Bond br_mid = ns == 2 ? mps->bonds[i + 2] : br;
   mps->bonds[i + 1] = nb;
   mps->sites[i] = std::move(A);
   env->R[i + 1].valid = false;
   tr.mark("site+C");
   env_update_left(env, i);
   tr.mark("env");
-  // guess for window i+1: C . B_{i+2}
-  if (i + 2 < mps->n) {
+  // keep_centre (two sites): psi := C, the one-site psi of site i+1 on bonds (i+1, i+2)
+  // (a site tensor's layout is the one-site layout)
+  if (keep_centre) {
+    B2_REQUIRE(ns == 2 && nroot == 1, B2_EINVAL, "internal: keep_centre");
+    psi = std::move(C.data);
+    return;
+  }
+  // guess for the next window: C . B_{i+ns}.  One-site: C(jt, 0 -> jr) B_{i+1}(jr, s -> jr')
+  // lands in the layout with the trivial site first, i.e. at the one-site offsets.
+  if (i + ns < mps->n) {
     PsiLayout nl;
-    nl.build(mps->bonds[i + 1], mps->bonds[i + 3]);
-    DevBuf np(c, sizeof(double) * std::max<int64_t>(nl.size, 1));
-    contract_two_sites(c, mps->bonds[i + 1], mps->bonds[i + 2], C, C.data.as<double>(),
-                       mps->sites[i + 2], mps->sites[i + 2].data.as<double>(), nl, np.as<double>(),
-                       flops);
+    nl.build(mps->bonds[i + 1], mps->bonds[i + 1 + ns], ns, ns == 1);
+    DevBuf np(c, sizeof(double) * std::max<int64_t>(nl.size * nroot, 1));
+    for (int rt = 0; rt < nroot; ++rt)
+      contract_two_sites(c, mps->bonds[i + 1], br_mid, C, C.data.as<double>() + rt * C.size,
+                         mps->sites[i + ns], mps->sites[i + ns].data.as<double>(), nl,
+                         np.as<double>() + rt * nl.size, flops);
     psi = std::move(np);
   }
 }
 
-// Backward split of window i: psi -> B_{i+1} (right-orthonormal, new bond i+1) and the guess
-// for window i-1.  Updates mps->bonds[i+1], mps->sites[i+1], R_{i+1}; writes the new psi.
-// With i == 0 and guess == false it only re-canonicalises (site 0 := C).
-void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
-                 double* flops, bool make_guess) {
+// Backward split of window win (site i): psi -> B_k (right-orthonormal, new bond k) with
+// k = i+1 for two sites and k = i for one, and the guess for the previous window of the same
+// width.  Updates mps->bonds[k], mps->sites[k], R_k; writes the new psi.  Two sites: rows
+// (jl, s1), columns (s2, jr).  One site: psi read with the trivial site first, (jl, 0, s, jr),
+// so the same code takes rows (jl) and columns (s, jr).  With a two-site window 0 and
+// guess == false it only re-canonicalises (site 0 := C).
+void split_right(b2_env_s* env, int win, DevBuf& psi, int M, double cutoff, double* discarded,
+                 double* flops, bool make_guess, double noise, int nroot, bool keep_centre) {
   Ctx* c = env->ctx;
+  const int i = win_site(win), ns = win_nsite(win);
+  const int k = i + ns - 1;
   Tracer tr(c, "split_right", i);
   b2_mps_s* mps = env->mps;
-  WindowProgram& wp = window_program(env, i);
-  const PsiLayout lay = wp.psi;
-  const Bond& bl = mps->bonds[i];
-  const Bond& br = mps->bonds[i + 2];
+  B2_REQUIRE(ns == 2 || (make_guess && i > 0), B2_EINVAL, "internal: one-site split at site 0");
+  WindowProgram& wp = window_program(env, win);
+  PsiLayout lay = wp.psi;
+  const Bond bl = mps->bonds[i];
+  const Bond br = mps->bonds[i + ns];
+  if (ns == 1) lay.build(bl, br, 1, true);
+  const int64_t n = lay.size;               // psi holds nroot states of this layout
+  const double wr = 1.0 / nroot;            // state-average weight
   std::map<int64_t, int> sidx;
   std::vector<RhoSector> secs;
   std::vector<QN> qs;
@@ -730,13 +1053,20 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   DevBuf evecs(c, sizeof(double) * std::max<int64_t>(tot, 1));
   // rho_q[(s2,jr),(s2',jr')] = sum_{(jl,s1) in q} psi(jl,s1,s2)^T psi(jl,s1,s2')
   GemmProgram prog;
-  for (auto& r : secs)
-    for (size_t a = 0; a < r.parts.size(); ++a)
-      for (size_t b = 0; b < r.parts.size(); ++b) {
+  std::vector<std::vector<int>> out_of(secs.size());
+  std::vector<std::pair<int, int>> part_of(size_t(br.size()) * 4, {-1, -1});   // (sector, part)
+  for (size_t j = 0; j < secs.size(); ++j)
+    for (size_t a = 0; a < secs[j].parts.size(); ++a)
+      part_of[size_t(secs[j].parts[a].first) * 4 + secs[j].parts[a].second] = {int(j), int(a)};
+  for (size_t j = 0; j < secs.size(); ++j)
+    for (size_t a = 0; a < secs[j].parts.size(); ++a)
+      for (size_t b = 0; b < secs[j].parts.size(); ++b) {
+        const RhoSector& r = secs[j];
         int jra = r.parts[a].first, sa = r.parts[a].second;
         int jrb = r.parts[b].first, sb = r.parts[b].second;
         int o = prog.add_out(1, r.off + int64_t(r.part_off[a]) * r.dim + r.part_off[b], br.m[jra],
                              br.m[jrb], r.dim, false);
+        out_of[j].push_back(o);
         for (int jl = 0; jl < bl.size(); ++jl)
           for (int s1 = 0; s1 < 4; ++s1) {
             if (!(bl.q[jl] + kSiteQ[s1] == r.q)) continue;
@@ -745,24 +1075,118 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
             const PsiBlock& A = lay.blocks[pa];
             const PsiBlock& B = lay.blocks[pb];
             if (A.jr != jra || B.jr != jrb) continue;
-            GemmTerm t{};
-            t.offP = A.off; t.bufP = 0; t.ldP = A.mr;    // op(P) = A^T [m_jra x m_jl]
-            t.offX = B.off; t.bufX = 0; t.ldX = B.mr;    // X [m_jl x m_jrb]
-            t.K1 = A.ml;
-            t.flags = kTwoOp | kTransP;
-            t.alpha = 1.0;
-            prog.add_term(o, t);
+            for (int rt = 0; rt < nroot; ++rt) {
+              GemmTerm t{};
+              t.offP = A.off + rt * n; t.bufP = 0; t.ldP = A.mr;    // op(P) = A^T [m_jra x m_jl]
+              t.offX = B.off + rt * n; t.bufX = 0; t.ldX = B.mr;    // X [m_jl x m_jrb]
+              t.K1 = A.ml;
+              t.flags = kTwoOp | kTransP;
+              t.alpha = wr;
+              prog.add_term(o, t);
+            }
           }
       }
+  // noise: P_w(jl, s1; s2', jr') = sum_{b, s2} c (-1)^{p(b) n(s2)} psi(jl, s1, s2, jr) R_b(jr' <- jr)^T
+  // with W of the kept site k (channels w on bond k, b on bond i+ns)
+  DevBuf pbuf;
+  if (noise > 0) {
+    const EnvBond& R = env->R[i + ns];
+    b2_mpo_s* mpo = env->mpo;
+    std::vector<NoiseBlock> nb_;
+    std::vector<std::pair<int, GemmTerm>> pterms;   // (block, term) of one state
+    std::unordered_map<int64_t, int> nidx;
+    const int64_t ncol = int64_t(4) * br.size();
+    GemmProgram pp;
+    int64_t psize = 0;                              // per state
+    for (const auto& e : mpo->W[k]) {
+      const int w = e.w, b = e.w2;
+      const bool pb = mpo->parity[i + ns][b] != 0;
+      for (int u = 0; u < 16; ++u) {
+        if (e.m[u] == 0) continue;
+        const int s2p = u / 4, s2 = u % 4;
+        const double sg = (pb && (kSiteN[s2] & 1)) ? -1.0 : 1.0;
+        for (const auto& P : lay.blocks) {
+          if (P.s2 != s2) continue;
+          const int rb = R.find(b, P.jr);
+          if (rb < 0) continue;
+          const int jrp = R.blocks[rb].jb;
+          const int col = jrp * 4 + s2p;
+          if (part_of[col].first < 0) continue;
+          const int row = P.jl * 4 + P.s1;
+          const int64_t key = (int64_t(w) * bl.size() * 4 + row) * ncol + col;
+          auto it = nidx.find(key);
+          int o;
+          if (it == nidx.end()) {
+            o = int(nb_.size());
+            nidx.emplace(key, o);
+            nb_.push_back({w, row, col, psize, P.ml, br.m[jrp]});
+            psize += int64_t(P.ml) * br.m[jrp];
+          } else {
+            o = it->second;
+          }
+          GemmTerm t{};
+          t.offP = P.off; t.bufP = 0; t.ldP = P.mr;                      // psi [m_jl x m_jr]
+          t.offX = R.blocks[rb].off; t.bufX = 3; t.ldX = P.mr;           // R_b [m_jr' x m_jr]
+          t.K1 = P.mr;
+          t.flags = kTwoOp | kTransQ;
+          t.alpha = e.m[u] * sg;
+          pterms.push_back({o, t});
+        }
+      }
+    }
+    if (psize > 0) {
+      const double sw = std::sqrt(wr);
+      for (int rt = 0; rt < nroot; ++rt)
+        for (const auto& b : nb_) pp.add_out(1, rt * psize + b.off, b.m_row, b.m_col, b.m_col, false);
+      for (int rt = 0; rt < nroot; ++rt)
+        for (auto bt : pterms) {
+          bt.second.offP += rt * n;
+          bt.second.alpha *= sw;
+          pp.add_term(rt * int(nb_.size()) + bt.first, bt.second);
+        }
+      pp.finalize(c);
+      pbuf.reset(c, sizeof(double) * size_t(psize) * nroot);
+      BufTable pt{};
+      pt.p[0] = psi.as<double>();
+      pt.p[1] = pbuf.as<double>();
+      pt.p[3] = R.data.as<double>();
+      pp.launch(c, pt);
+      *flops += pp.flops;
+      const double trN = norm2_device(c, pbuf.as<double>(), psize * nroot);
+      if (trN > 0) {
+        // Gram terms per environment row: rho[(col x), (col y)] += scale P_x^T P_y
+        std::map<int64_t, std::vector<int>> by_row;   // key: w * (4 |bond i|) + row
+        for (size_t x = 0; x < nb_.size(); ++x)
+          by_row[int64_t(nb_[x].w) * bl.size() * 4 + nb_[x].row].push_back(int(x));
+        for (auto& kv : by_row)
+          for (int x : kv.second)
+            for (int y : kv.second) {
+              const auto px = part_of[nb_[x].col], py = part_of[nb_[y].col];
+              if (px.first != py.first) continue;
+              const int np_ = int(secs[px.first].parts.size());
+              for (int rt = 0; rt < nroot; ++rt) {
+                GemmTerm t{};
+                t.offP = rt * psize + nb_[x].off; t.bufP = 2; t.ldP = nb_[x].m_col;   // P_x^T
+                t.offX = rt * psize + nb_[y].off; t.bufX = 2; t.ldX = nb_[y].m_col;
+                t.K1 = nb_[x].m_row;
+                t.flags = kTwoOp | kTransP;
+                t.alpha = noise / trN;
+                prog.add_term(out_of[px.first][size_t(px.second) * np_ + py.second], t);
+              }
+            }
+      }
+    }
+  }
   prog.finalize(c);
   BufTable bt{};
   bt.p[0] = psi.as<double>();
   bt.p[1] = rho.as<double>();
+  bt.p[2] = pbuf.as<double>();
   prog.launch(c, bt);
   *flops += prog.flops;
   tr.mark("rho");
   std::vector<int> kept = eig_and_select(c, secs, rho, evals, evecs, M, cutoff, discarded,
-                                         &env->rho_cache[2 * i + 1]);
+                                         &env->rho_cache[4 * i + 2 * (ns == 1) + 1]);
   tr.mark("eig+select");
 
   Bond nb;
@@ -812,10 +1236,11 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   // C(jl, s1 -> jt) = sum_s2 psi(jl,s1,s2) B(jt,s2,jr)^T
   SiteTensor C;
   C.build(bl, nb);
-  C.data.reset(c, sizeof(double) * std::max<int64_t>(C.size, 1));
+  C.data.reset(c, sizeof(double) * std::max<int64_t>(C.size * nroot, 1));   // one C per state
   GemmProgram pc;
+  for (int rt = 0; rt < nroot; ++rt)
   for (const auto& cbk : C.blocks) {
-    int o = pc.add_out(1, cbk.off, cbk.ml, cbk.mr, cbk.mr, false);
+    int o = pc.add_out(1, rt * C.size + cbk.off, cbk.ml, cbk.mr, cbk.mr, false);
     for (int s2 = 0; s2 < 4; ++s2) {
       int pb = lay.find(cbk.jl, cbk.s, s2);
       if (pb < 0) continue;
@@ -824,7 +1249,7 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
       if (bb < 0 || Bt.blocks[bb].jr != P.jr) continue;
       const SiteBlock& Bb = Bt.blocks[bb];
       GemmTerm t{};
-      t.offP = P.off; t.bufP = 0; t.ldP = P.mr;
+      t.offP = P.off + rt * n; t.bufP = 0; t.ldP = P.mr;
       t.offX = Bb.off; t.bufX = 2; t.ldX = Bb.mr;   // op(X) = B^T [m_jr x m_jt]
       t.K1 = P.mr;
       t.flags = kTwoOp | kTransQ;
@@ -840,19 +1265,24 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   pc.launch(c, bc);
   *flops += pc.flops;
 
-  mps->bonds[i + 1] = nb;
-  mps->sites[i + 1] = std::move(Bt);
-  env->L[i + 1].valid = false;
+  mps->bonds[k] = nb;
+  mps->sites[k] = std::move(Bt);
+  env->L[k].valid = false;
   tr.mark("site+C");
-  env_update_right(env, i + 1);
+  env_update_right(env, k);
   tr.mark("env");
-  if (make_guess && i > 0) {
+  if (keep_centre) {   // two sites: psi := C, the one-site psi of site i on bonds (i, i+1)
+    B2_REQUIRE(ns == 2 && nroot == 1, B2_EINVAL, "internal: keep_centre");
+    psi = std::move(C.data);
+  } else if (make_guess && i > 0) {
+    // A_{i-1} . C on bonds (i-1, i+ns-1); bl is bond i as A_{i-1} and C knew it
     PsiLayout nl;
-    nl.build(mps->bonds[i - 1], mps->bonds[i + 1]);
-    DevBuf np(c, sizeof(double) * std::max<int64_t>(nl.size, 1));
-    contract_two_sites(c, mps->bonds[i - 1], mps->bonds[i], mps->sites[i - 1],
-                       mps->sites[i - 1].data.as<double>(), C, C.data.as<double>(), nl,
-                       np.as<double>(), flops);
+    nl.build(mps->bonds[i - 1], mps->bonds[k], ns);
+    DevBuf np(c, sizeof(double) * std::max<int64_t>(nl.size * nroot, 1));
+    for (int rt = 0; rt < nroot; ++rt)
+      contract_two_sites(c, mps->bonds[i - 1], bl, mps->sites[i - 1],
+                         mps->sites[i - 1].data.as<double>(), C, C.data.as<double>() + rt * C.size,
+                         nl, np.as<double>() + rt * nl.size, flops);
     psi = std::move(np);
   } else {
     // centre stays on site i: it holds C
@@ -861,7 +1291,172 @@ void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double
   }
 }
 
+// ------------------------------------------------------------------- TDVP
+// psi <- exp(-t H_eff) psi / |exp(-t H_eff) psi| for window win by the Krylov (Lanczos)
+// method: orthonormal basis V of span{psi, H psi, ...} (each new vector orthogonalised twice
+// against all previous ones), T = V^T H V (FP64 products; T from the same V.W dot products as
+// Davidson's Rayleigh-Ritz), its eigen-decomposition by the Jacobi kernel, and
+// c = exp(-t (T - lambda_min)) e_1 (k_krylov_coef).  Stops when the next vector's weight
+// beta_k |c_k| is <= tol |c|, when the space is exhausted (beta <= 1e-14 max(1, |lambda|))
+// or at max_k vectors; psi = V c normalised (imaginary time does not keep the norm and only
+// the direction is used).  One host synchronisation per Krylov vector.
+static void krylov_exp(b2_env_s* env, int win, double* psi, double t, double tol, int max_k,
+                       double* flops, int* n_matvec) {
+  Ctx* c = env->ctx;
+  WindowProgram& wp = window_program(env, win);
+  const int64_t n = wp.psi.size;
+  B2_REQUIRE(n > 0, B2_EINVAL, "empty wavefunction");
+  const int kmax = std::max(2, std::min(max_k > 0 ? max_k : 40, 64));
+  DevBuf V(c, sizeof(double) * n * kmax), W(c, sizeof(double) * n * kmax);
+  const int kPart = 256 * 16;
+  DevBuf small(c, sizeof(double) * (kPart + 4 * kmax * kmax + 4 * kmax + 16));
+  double* part = small.as<double>();
+  double* VW = part + kPart;
+  double* G = VW + kmax * kmax;
+  double* evecs = G + kmax * kmax;
+  double* evals = evecs + kmax * kmax;
+  double* cvec = evals + kmax;
+  double* stats = cvec + 2 * kmax;   // |c|^2, lambda_min, max |lambda|, beta^2, c_last
+  double* Vp = V.as<double>();
+  double* Wp = W.as<double>();
+  std::vector<int> dims_h(kmax + 1);
+  for (int x = 0; x <= kmax; ++x) dims_h[x] = x;
+  int64_t offs_h[2] = {0, 0};
+  DevBuf d_dims, d_offs(c, sizeof(int64_t) * 2);
+  upload(c, d_dims, dims_h);
+  B2_CUDA(cudaMemcpyAsync(d_offs.ptr, offs_h, sizeof(offs_h), cudaMemcpyHostToDevice, c->stream));
+  b2k::launch_multidot(1, psi, n, psi, n, part, stats + 3, 1, c->stream);
+  B2_CUDA(cudaMemcpyAsync(Vp, psi, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  b2k::launch_scale_inv_sqrt(Vp, n, stats + 3, c->stream);
+  int m = 0;
+  double fl = 0;
+  for (;;) {
+    double* vm = Vp + int64_t(m) * n;
+    double* wm = Wp + int64_t(m) * n;
+    heff_apply(env, win, vm, wm, 0.0, &fl, B2_FP64);
+    if (flops) *flops += fl;
+    if (n_matvec) ++*n_matvec;
+    b2k::launch_multidot(m + 1, Vp, n, wm, n, part, VW + m, kmax, c->stream);
+    if (m > 0) b2k::launch_multidot(m, Wp, n, vm, n, part, VW + int64_t(m) * kmax, 1, c->stream);
+    ++m;
+    b2k::launch_symmetrize(m, VW, kmax, G, c->stream);
+    b2k::launch_jacobi(1, d_dims.as<int>() + m, d_offs.as<int64_t>(), d_offs.as<int64_t>(), G,
+                       evals, evecs, nullptr, d_offs.as<int64_t>(), m, c->stream);
+    b2k::launch_krylov_coef(m, evecs, evals, t, cvec, stats, c->stream);
+    if (m >= kmax) break;
+    // next direction: H v_{m-1} orthogonalised twice against V
+    double* vn = Vp + int64_t(m) * n;
+    B2_CUDA(cudaMemcpyAsync(vn, wm, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+      b2k::launch_multidot(m, Vp, n, vn, n, part, cvec + kmax, 1, c->stream);
+      b2k::launch_multiaxpy(m, Vp, n, cvec + kmax, vn, n, -1.0, c->stream);
+    }
+    b2k::launch_multidot(1, vn, n, vn, n, part, stats + 3, 1, c->stream);
+    double h[4];
+    B2_CUDA(cudaMemcpyAsync(h, stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+    double clast = 0;
+    B2_CUDA(cudaMemcpyAsync(&clast, cvec + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    B2_REQUIRE(std::isfinite(h[0]) && std::isfinite(h[3]), B2_ENOCONV, "Krylov exponential: non-finite value");
+    const double beta = std::sqrt(std::max(h[3], 0.0));
+    if (beta * std::fabs(clast) <= tol * std::sqrt(h[0]) || beta <= 1e-14 * std::max(1.0, h[2]))
+      break;
+    b2k::launch_scale_inv_sqrt(vn, n, stats + 3, c->stream);
+  }
+  B2_CUDA(cudaMemsetAsync(psi, 0, sizeof(double) * n, c->stream));
+  b2k::launch_multiaxpy(m, Vp, n, cvec, psi, n, 1.0, c->stream);
+  b2k::launch_multidot(1, psi, n, psi, n, part, stats + 3, 1, c->stream);
+  b2k::launch_scale_inv_sqrt(psi, n, stats + 3, c->stream);
+  B2_CUDA(cudaGetLastError());
+}
+
+// Imaginary-time two-site TDVP (projector splitting, second order; Sec. 2.7.3): per step a
+// forward half over windows 0..n-2 and a backward half n-2..0, each evolving the two-site psi
+// by exp(-tau/2 H2), splitting it (truncated like a sweep split) and evolving the one-site
+// remainder backwards by exp(+tau/2 H1) on the one-site window before contracting it with the
+// next site tensor.  Starts from and returns to an MPS centred at site 0.
+void tdvp(b2_env_s* env, const b2_tdvp_opts& o, b2_tdvp_result* res) {
+  Ctx* c = env->ctx;
+  b2_mps_s* mps = env->mps;
+  const int n = mps->n;
+  B2_REQUIRE(n >= 3, B2_EINVAL, "TDVP needs at least three sites");
+  B2_REQUIRE(mps->center == 0, B2_EINVAL, "TDVP needs an MPS centred at site 0");
+  B2_REQUIRE(env->L[0].valid, B2_EINVAL, "env not initialised at centre 0");
+  for (int k = 2; k <= n; ++k) B2_REQUIRE(env->R[k].valid, B2_EINVAL, "env not initialised at centre 0");
+  B2_REQUIRE(o.bond_dim >= 1 && std::isfinite(o.tau) && o.tau > 0, B2_EINVAL, "bad TDVP options");
+  const double cutoff = o.trunc_cutoff >= 0 ? o.trunc_cutoff : 1e-14;
+  const double ktol = o.krylov_tol > 0 ? o.krylov_tol : 1e-12;
+  const int kmax = o.krylov_max > 0 ? o.krylov_max : 40;
+  const double h = 0.5 * o.tau;
+  auto two_site_from = [&](int i, const SiteTensor& X, const double* xd, const SiteTensor& Y,
+                           const double* yd, double* fl) {
+    WindowProgram& wp = window_program(env, i);
+    DevBuf np(c, sizeof(double) * std::max<int64_t>(wp.psi.size, 1));
+    contract_two_sites(c, mps->bonds[i], mps->bonds[i + 1], X, xd, Y, yd, wp.psi, np.as<double>(), fl);
+    return np;
+  };
+  double fl0 = 0;
+  DevBuf psi = two_site_from(0, mps->sites[0], mps->sites[0].data.as<double>(), mps->sites[1],
+                             mps->sites[1].data.as<double>(), &fl0);
+  for (int step = 0; step < o.n_steps; ++step) {
+    B2_CUDA(cudaStreamSynchronize(c->stream));
+    auto t0 = std::chrono::steady_clock::now();
+    b2_tdvp_result r{};
+    double dw = 0, other = 0;
+    for (int i = 0; i <= n - 2; ++i) {
+      krylov_exp(env, i, psi.as<double>(), h, ktol, kmax, &r.matvec_flops, &r.n_matvec);
+      if (i < n - 2) {
+        split_left(env, i, psi, o.bond_dim, cutoff, &dw, &other, 0.0, 1, true);
+        r.discarded_weight = std::max(r.discarded_weight, dw);
+        krylov_exp(env, (i + 1) | kOneSite, psi.as<double>(), -h, ktol, kmax, &r.matvec_flops,
+                   &r.n_matvec);
+        SiteTensor X;   // layout of the one-site psi of site i+1
+        X.build(mps->bonds[i + 1], mps->bonds[i + 2]);
+        psi = two_site_from(i + 1, X, psi.as<double>(), mps->sites[i + 2],
+                            mps->sites[i + 2].data.as<double>(), &other);
+      }
+    }
+    for (int i = n - 2; i >= 0; --i) {
+      krylov_exp(env, i, psi.as<double>(), h, ktol, kmax, &r.matvec_flops, &r.n_matvec);
+      if (i > 0) {
+        split_right(env, i, psi, o.bond_dim, cutoff, &dw, &other, false, 0.0, 1, true);
+        r.discarded_weight = std::max(r.discarded_weight, dw);
+        krylov_exp(env, i | kOneSite, psi.as<double>(), -h, ktol, kmax, &r.matvec_flops,
+                   &r.n_matvec);
+        SiteTensor Y;   // layout of the one-site psi of site i
+        Y.build(mps->bonds[i], mps->bonds[i + 1]);
+        psi = two_site_from(i - 1, mps->sites[i - 1], mps->sites[i - 1].data.as<double>(), Y,
+                            psi.as<double>(), &other);
+      }
+    }
+    // energy of the (normalised) window-0 psi
+    {
+      WindowProgram& wp = window_program(env, 0);
+      const int64_t nn = wp.psi.size;
+      DevBuf hp(c, sizeof(double) * std::max<int64_t>(nn, 1)), sc(c, sizeof(double) * (256 * 16 + 1));
+      double fl = 0;
+      heff_apply(env, 0, psi.as<double>(), hp.as<double>(), 0.0, &fl, B2_FP64);
+      b2k::launch_multidot(1, psi.as<double>(), nn, hp.as<double>(), nn, sc.as<double>(),
+                           sc.as<double>() + 256 * 16, 1, c->stream);
+      B2_CUDA(cudaMemcpyAsync(&r.energy, sc.as<double>() + 256 * 16, sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+      sync(c);
+    }
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (auto& b : mps->bonds) r.max_bond = std::max(r.max_bond, b.total);
+    if (res) res[step] = r;
+  }
+  double dw = 0, fl = 0;
+  split_right(env, 0, psi, 1 << 30, cutoff, &dw, &fl, false);
+  sync(c);
+}
+
 // ------------------------------------------------------------------------ sweep
+// Between sweeps the centre is at site 0: the two-site psi of window 0 (width 2; R_2 and
+// L_0 exist) or the one-site psi of site 0 (width 1; R_1 exists), which has the layout of
+// site tensor 0 on bonds (0, 1).  Changing the width at the start of a sweep (Sec. 2.1.2:
+// mixing the one-site and two-site algorithms): 2 -> 1 splits the window-0 psi backward with
+// the entering sweep's M and cutoff (B_1, R_1, centre C); 1 -> 2 contracts psi with B_1.
 void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
   Ctx* c = env->ctx;
   b2_mps_s* mps = env->mps;
@@ -869,6 +1464,20 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
   B2_REQUIRE(mps->center == 0, B2_EINVAL, "sweep needs an MPS centred at site 0");
   B2_REQUIRE(env->L[0].valid, B2_EINVAL, "env not initialised at centre 0");
   for (int k = 2; k <= n; ++k) B2_REQUIRE(env->R[k].valid, B2_EINVAL, "env not initialised at centre 0");
+  if (o.dots)
+    for (int sw = 0; sw < o.n_sweeps; ++sw)
+      B2_REQUIRE(o.dots[sw] == 1 || o.dots[sw] == 2, B2_EINVAL, "dots entries must be 1 or 2");
+  if (o.noise)
+    for (int sw = 0; sw < o.n_sweeps; ++sw)
+      B2_REQUIRE(o.noise[sw] >= 0 && std::isfinite(o.noise[sw]), B2_EINVAL, "noise must be >= 0");
+  const int nr = o.n_roots > 1 ? o.n_roots : 1;   // state-averaged roots
+  B2_REQUIRE(nr <= B2_MAX_ROOTS, B2_EINVAL, "n_roots above B2_MAX_ROOTS");
+  if (nr > 1) {
+    B2_REQUIRE(o.prec == B2_FP64, B2_EUNSUPPORTED, "state averaging runs FP64 products only");
+    if (o.dots)
+      for (int sw = 0; sw < o.n_sweeps; ++sw)
+        B2_REQUIRE(o.dots[sw] == 2, B2_EUNSUPPORTED, "state averaging runs two-site sweeps only");
+  }
   b2_dav_opts dop;
   dop.max_iter = o.dav_max_iter > 0 ? o.dav_max_iter : 30;
   dop.max_subspace = o.max_subspace > 0 ? o.max_subspace : 30;
@@ -876,20 +1485,43 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
   dop.prec = o.prec;
   dop.refine_max = 0;
   const double cutoff = o.trunc_cutoff >= 0 ? o.trunc_cutoff : 1e-14;
-  // psi of window 0
   DevBuf psi;
-  {
-    WindowProgram& wp = window_program(env, 0);
-    psi.reset(c, sizeof(double) * std::max<int64_t>(wp.psi.size, 1));
-    double fl = 0;
-    contract_two_sites(c, mps->bonds[0], mps->bonds[1], mps->sites[0], mps->sites[0].data.as<double>(),
-                       mps->sites[1], mps->sites[1].data.as<double>(), wp.psi, psi.as<double>(), &fl);
-  }
+  int width = 0;   // width of the centre psi (0: none formed yet, the MPS holds it)
+  auto enter = [&](int ns, int M) {
+    if (ns == width) return;
+    double dw = 0, fl = 0;
+    if (ns == 2) {
+      WindowProgram& wp = window_program(env, 0);
+      DevBuf np(c, sizeof(double) * std::max<int64_t>(wp.psi.size * nr, 1));
+      if (nr > 1)   // further states start from zero (completed by the Davidson rule)
+        B2_CUDA(cudaMemsetAsync(np.ptr, 0, np.bytes, c->stream));
+      SiteTensor X;   // layout of the centre on bonds (0, 1); data: the MPS's or psi
+      X.build(mps->bonds[0], mps->bonds[1]);
+      const double* xd = width == 1 ? psi.as<double>() : mps->sites[0].data.as<double>();
+      contract_two_sites(c, mps->bonds[0], mps->bonds[1], X, xd, mps->sites[1],
+                         mps->sites[1].data.as<double>(), wp.psi, np.as<double>(), &fl);
+      psi = std::move(np);
+    } else {
+      if (width == 2) split_right(env, 0, psi, M, cutoff, &dw, &fl, false);   // site 0 := C
+      if (!env->R[1].valid) env_update_right(env, 1);
+      const SiteTensor& s0 = mps->sites[0];
+      DevBuf np(c, sizeof(double) * std::max<int64_t>(s0.size, 1));
+      if (s0.size > 0)
+        B2_CUDA(cudaMemcpyAsync(np.ptr, s0.data.ptr, sizeof(double) * size_t(s0.size),
+                                cudaMemcpyDeviceToDevice, c->stream));
+      psi = std::move(np);
+    }
+    width = ns;
+  };
   for (int sw = 0; sw < o.n_sweeps; ++sw) {
     B2_CUDA(cudaStreamSynchronize(c->stream));
     auto t0 = std::chrono::steady_clock::now();
     const int M = o.bond_dims[sw];
     B2_REQUIRE(M >= 1, B2_EINVAL, "bond dimension must be positive");
+    const int ns = o.dots ? o.dots[sw] : 2;
+    const int flag = ns == 1 ? kOneSite : 0;
+    const double nz = o.noise ? o.noise[sw] : 0.0;
+    enter(ns, M);
     b2_sweep_result r{};
     double dw = 0, e = 0;
     auto now = [] { return std::chrono::steady_clock::now(); };
@@ -898,26 +1530,38 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
     };
     auto solve = [&](int i) {
       auto ta = now();
-      DavidsonResult d = davidson(env, i, psi.as<double>(), dop);
+      if (nr > 1) {
+        int nmv = 0;
+        double r2 = 0, fl = 0;
+        std::vector<double> th = davidson_roots(env, i, psi.as<double>(), nr, dop, &nmv, &r2, &fl);
+        r.matvec_flops += fl;
+        r.n_matvec += nmv;
+        e = th[0];
+        for (int j = 0; j < nr; ++j) r.root_energy[j] = th[j];
+      } else {
+        DavidsonResult d = davidson(env, i | flag, psi.as<double>(), dop);
+        r.matvec_flops += d.flops;
+        r.n_matvec += d.n_matvec;
+        e = d.energy;
+        r.root_energy[0] = e;
+      }
       r.t_davidson += secs(ta, now());
-      r.matvec_flops += d.flops;
-      r.n_matvec += d.n_matvec;
-      e = d.energy;
     };
-    for (int i = 0; i <= n - 2; ++i) {
+    const int last = n - ns;   // last window site
+    for (int i = 0; i <= last; ++i) {
       solve(i);
-      if (i < n - 2) {
+      if (i < last) {
         auto ta = now();
-        split_left(env, i, psi, M, cutoff, &dw, &r.other_flops);
+        split_left(env, i | flag, psi, M, cutoff, &dw, &r.other_flops, nz, nr);
         r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
     }
-    for (int i = n - 2; i >= 0; --i) {
+    for (int i = last; i >= 0; --i) {
       solve(i);
       if (i > 0) {
         auto ta = now();
-        split_right(env, i, psi, M, cutoff, &dw, &r.other_flops, true);
+        split_right(env, i | flag, psi, M, cutoff, &dw, &r.other_flops, true, nz, nr);
         r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
@@ -928,9 +1572,19 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
     for (auto& b : mps->bonds) r.max_bond = std::max(r.max_bond, b.total);
     if (res) res[sw] = r;
   }
-  // leave the MPS centred at site 0: B_1 from psi of window 0 without truncation
-  double dw = 0, fl = 0;
-  split_right(env, 0, psi, 1 << 30, 0.0, &dw, &fl, false);
+  // leave the MPS centred at site 0: two sites, B_1 from psi of window 0 without a bond
+  // limit (states of relative weight <= cutoff, numerically zero, dropped as in every
+  // split); one site, psi is site tensor 0
+  if (width == 2) {
+    double dw = 0, fl = 0;
+    split_right(env, 0, psi, 1 << 30, cutoff, &dw, &fl, false, 0.0, nr);
+  } else if (width == 1) {
+    SiteTensor s0;
+    s0.build(mps->bonds[0], mps->bonds[1]);
+    s0.data = std::move(psi);
+    mps->sites[0] = std::move(s0);
+    mps->center = 0;
+  }
   sync(c);
 }
 

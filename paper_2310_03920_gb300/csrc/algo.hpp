@@ -24,10 +24,23 @@ void contract_two_sites(Ctx* c, const Bond& ba, const Bond& bb, const SiteTensor
                         const double* xd, const SiteTensor& Y, const double* yd,
                         const PsiLayout& lay, double* out, double* flops);
 DavidsonResult davidson(b2_env_s* env, int site, double* psi, const b2_dav_opts& o);
-void split_left(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
-                double* flops);
-void split_right(b2_env_s* env, int i, DevBuf& psi, int M, double cutoff, double* discarded,
-                 double* flops, bool make_guess);
+// The n_roots lowest eigenpairs (FP64 block Davidson, see algo.cpp); returns the eigenvalues.
+std::vector<double> davidson_roots(b2_env_s* env, int win, double* psis, int n_roots,
+                                   const b2_dav_opts& o, int* n_matvec, double* max_resid2,
+                                   double* flops);
+// Splits of the window with id win (a site, or site | kOneSite), see algo.cpp.
+// noise: weight of the perturbative noise added to the density matrix (0: none).
+// nroot: psi holds that many states of the window layout one after the other; the density
+// matrix is their average (weights 1/nroot) and each gets its own remainder and guess.
+// keep_centre (two-site windows, one state): psi becomes the split remainder C itself, the
+// one-site psi of the centre site (TDVP evolves it before moving on).
+void split_left(b2_env_s* env, int win, DevBuf& psi, int M, double cutoff, double* discarded,
+                double* flops, double noise = 0.0, int nroot = 1, bool keep_centre = false);
+void split_right(b2_env_s* env, int win, DevBuf& psi, int M, double cutoff, double* discarded,
+                 double* flops, bool make_guess, double noise = 0.0, int nroot = 1,
+                 bool keep_centre = false);
+// Imaginary-time two-site TDVP steps (see algo.cpp, b2_tdvp).
+void tdvp(b2_env_s* env, const b2_tdvp_opts& o, b2_tdvp_result* res);
 void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res);
 // Many independent problems in lockstep, one grouped H_eff launch per Davidson iteration
 // (batch.cpp); per problem identical to davidson / sweep.

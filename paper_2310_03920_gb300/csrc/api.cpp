@@ -224,9 +224,19 @@ int b2_psi_from_mps(b2_ctx ctx, b2_env env, int site, double* psi) {
     ensure_device(ctx);
     auto& wp = b2::window_program(env, site);
     b2_mps_s* mps = env->mps;
-    b2::contract_two_sites(&ctx->c, mps->bonds[site], mps->bonds[site + 1], mps->sites[site],
-                           mps->sites[site].data.as<double>(), mps->sites[site + 1],
-                           mps->sites[site + 1].data.as<double>(), wp.psi, psi, nullptr);
+    const int i = b2::win_site(site);
+    if (b2::win_nsite(site) == 1) {
+      // the one-site psi has the layout of the site tensor itself
+      const b2::SiteTensor& st = mps->sites[i];
+      B2_REQUIRE(st.size == wp.psi.size, B2_EINVAL, "internal: one-site layout");
+      if (st.size > 0)
+        B2_CUDA(cudaMemcpyAsync(psi, st.data.ptr, sizeof(double) * size_t(st.size),
+                                cudaMemcpyDeviceToDevice, ctx->c.stream));
+    } else {
+      b2::contract_two_sites(&ctx->c, mps->bonds[i], mps->bonds[i + 1], mps->sites[i],
+                             mps->sites[i].data.as<double>(), mps->sites[i + 1],
+                             mps->sites[i + 1].data.as<double>(), wp.psi, psi, nullptr);
+    }
   });
 }
 
@@ -276,6 +286,17 @@ int b2_sweep(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_sweep_opts
     B2_REQUIRE(env->mpo == mpo && env->mps == mps, B2_EINVAL, "env was made for another mpo/mps");
     ensure_device(ctx);
     b2::sweep(env, *opts, per_sweep);
+  });
+}
+
+int b2_tdvp(b2_ctx ctx, b2_mpo mpo, b2_mps mps, b2_env env, const b2_tdvp_opts* opts,
+            b2_tdvp_result* per_step) {
+  return guarded(ctx, [&] {
+    check_env(ctx, env);
+    B2_REQUIRE(opts && opts->n_steps >= 0, B2_EINVAL, "bad TDVP options");
+    B2_REQUIRE(env->mpo == mpo && env->mps == mps, B2_EINVAL, "env was made for another mpo/mps");
+    ensure_device(ctx);
+    b2::tdvp(env, *opts, per_step);
   });
 }
 

@@ -345,6 +345,13 @@ std::vector<DavidsonResult> davidson_batched(Ctx* c, const std::vector<b2_env_s*
 void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_opts& o,
                    b2_sweep_result* res, const int* dims_per_problem) {
   const int np = int(envs.size());
+  if (o.dots)
+    for (int sw = 0; sw < o.n_sweeps; ++sw)
+      B2_REQUIRE(o.dots[sw] == 2, B2_EUNSUPPORTED, "batched sweeps are two-site only");
+  if (o.noise)
+    for (int sw = 0; sw < o.n_sweeps; ++sw)
+      B2_REQUIRE(o.noise[sw] == 0, B2_EUNSUPPORTED, "batched sweeps take no noise");
+  B2_REQUIRE(o.n_roots <= 1, B2_EUNSUPPORTED, "batched sweeps solve for one root");
   b2_dav_opts dop;
   dop.max_iter = o.dav_max_iter > 0 ? o.dav_max_iter : 30;
   dop.max_subspace = o.max_subspace > 0 ? o.max_subspace : 30;
@@ -428,7 +435,7 @@ void sweep_batched(Ctx* c, const std::vector<b2_env_s*>& envs, const b2_sweep_op
   // leave every MPS centred at site 0 (as the single-problem sweep does)
   for (int p = 0; p < np; ++p) {
     double dw = 0, fl = 0;
-    split_right(envs[p], 0, psi[p], 1 << 30, 0.0, &dw, &fl, false);
+    split_right(envs[p], 0, psi[p], 1 << 30, cutoff, &dw, &fl, false);
   }
   B2_CUDA(cudaStreamSynchronize(c->stream));
 }

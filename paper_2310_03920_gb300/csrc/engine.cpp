@@ -181,10 +181,22 @@ void EnvBond::layout(const Bond& b, const std::vector<QN>& dq) {
     }
 }
 
-void PsiLayout::build(const Bond& bl, const Bond& br) {
+void PsiLayout::build(const Bond& bl, const Bond& br, int nsite, bool trivial_first) {
   blocks.clear();
   lookup.assign(size_t(bl.size()) * 16, -1);
   size = 0;
+  if (nsite == 1) {
+    for (int jl = 0; jl < bl.size(); ++jl)
+      for (int s = 0; s < 4; ++s) {
+        int jr = br.find(bl.q[jl] + kSiteQ[s]);
+        if (jr < 0) continue;
+        const int s1 = trivial_first ? 0 : s, s2 = trivial_first ? s : 0;
+        lookup[(size_t(jl) * 4 + s1) * 4 + s2] = int(blocks.size());
+        blocks.push_back({jl, s1, s2, jr, bl.m[jl], br.m[jr], size});
+        size += int64_t(bl.m[jl]) * br.m[jr];
+      }
+    return;
+  }
   for (int jl = 0; jl < bl.size(); ++jl)
     for (int s1 = 0; s1 < 4; ++s1)
       for (int s2 = 0; s2 < 4; ++s2) {
@@ -422,36 +434,53 @@ struct Edge {
 };
 }  // namespace
 
-static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
+static void build_window(b2_env_s* env, int win, WindowProgram& wp) {
   b2_mpo_s* mpo = env->mpo;
   b2_mps_s* mps = env->mps;
   Ctx* c = env->ctx;
+  const int i = win_site(win), ns = win_nsite(win);
   const EnvBond& L = env->L[i];
-  const EnvBond& R = env->R[i + 2];
+  const EnvBond& R = env->R[i + ns];
   const Bond& bl = mps->bonds[i];
-  const Bond& br = mps->bonds[i + 2];
+  const Bond& br = mps->bonds[i + ns];
   wp = WindowProgram();
+  wp.win = win;
   wp.site = i;
+  wp.nsite = ns;
   wp.ver_l = L.version;
   wp.ver_r = R.version;
-  wp.psi.build(bl, br);
+  wp.psi.build(bl, br, ns);
 
   // Two-site operator entries grouped by local pattern (u, v), u = 4 s1' + s2',
   // v = 4 s1 + s2: sum over w' of W_i[a,w']_{s1's1} W_{i+1}[w',b]_{s2's2}, with the sign of
   // moving the site-(i+1) operator past s1 and the right part past s1 s2 folded in.  Flat
   // edge lists per pattern; duplicates (several w' joining the same a, b) are merged after
   // a stable sort, so they are summed in generation order.
-  std::vector<std::vector<int>> byw(mpo->D[i + 1]);
-  for (size_t e = 0; e < mpo->W[i + 1].size(); ++e) byw[mpo->W[i + 1][e].w].push_back(int(e));
+  // One-site window: W_i[a,b]_{s's} alone with the sign of moving the right part past s,
+  // at patterns (4 s', 4 s) (the trivial second site in state 0).
   std::vector<std::vector<Edge>> pat(256);
-  for (const auto& e1 : mpo->W[i]) {
+  if (ns == 1)
+    for (const auto& e1 : mpo->W[i]) {
+      const int pb = mpo->parity[i + 1][e1.w2];
+      for (int a1 = 0; a1 < 16; ++a1) {
+        if (e1.m[a1] == 0) continue;
+        const int s1p = a1 / 4, s1 = a1 % 4;
+        const double sign = (pb && par_n(kSiteN[s1])) ? -1.0 : 1.0;
+        pat[(s1p * 4) * 16 + s1 * 4].push_back({e1.w, e1.w2, sign * e1.m[a1]});
+      }
+    }
+  std::vector<std::vector<int>> byw(ns == 2 ? mpo->D[i + 1] : 0);
+  if (ns == 2)
+    for (size_t e = 0; e < mpo->W[i + 1].size(); ++e) byw[mpo->W[i + 1][e].w].push_back(int(e));
+  static const std::vector<b2_mpo_s::Entry> kNoEntries;
+  for (const auto& e1 : ns == 2 ? mpo->W[i] : kNoEntries) {
     int nz1[16], n1 = 0;
     for (int a1 = 0; a1 < 16; ++a1)
       if (e1.m[a1] != 0) nz1[n1++] = a1;
     for (int e2i : byw[e1.w2]) {
       const auto& e2 = mpo->W[i + 1][e2i];
       const int p2 = op_parity(e2.m);
-      const int pb = mpo->parity[i + 2][e2.w2];
+      const int pb = mpo->parity[i + ns][e2.w2];
       for (int k1 = 0; k1 < n1; ++k1) {
         const int a1 = nz1[k1];
         const double x1 = e1.m[a1];
@@ -495,7 +524,7 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     bool block_h = false;
   };
   std::vector<Pending> pending;
-  const int Da = mpo->D[i], Db = mpo->D[i + 2];
+  const int Da = mpo->D[i], Db = mpo->D[i + ns];
   // The two block-Hamiltonian terms, L_H (x) 1 (x) R_H (left block's Hamiltonian, right
   // block's identity) and L_I (x) 1 (x) R_I (the reverse), carry the energy scale of H_eff;
   // they are kept out of the precombination as terms of their own (flag kBlockH) so that the
@@ -506,7 +535,7 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     auto& edges = pat[v * 16 + v];
     for (int which = 0; which < 2; ++which) {
       const int a = which ? mpo->chan_H[i] : mpo->chan_I[i];
-      const int b = which ? mpo->chan_H[i + 2] : mpo->chan_I[i + 2];
+      const int b = which ? mpo->chan_H[i + ns] : mpo->chan_I[i + ns];
       if (a < 0 || b < 0) continue;
       for (size_t k = 0; k < edges.size(); ++k)
         if (edges[k].a == a && edges[k].b == b) {
@@ -664,14 +693,14 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
     for (const auto& e : block_h_edges[v]) dedges[v].push_back(e);
   for (int v = 0; v < 16; ++v)
     for (const auto& e : pat[v * 16 + v])
-      if (mpo->dq[i][e.a] == QN{0, 0} && mpo->dq[i + 2][e.b] == QN{0, 0}) dedges[v].push_back(e);
+      if (mpo->dq[i][e.a] == QN{0, 0} && mpo->dq[i + ns][e.b] == QN{0, 0}) dedges[v].push_back(e);
   {
     // channel rows of the diagonal buffers
     std::vector<int> ka(Da, -1), kb(Db, -1);
     int KA = 0, KB = 0;
     for (int v = 0; v < 16; ++v)
       for (const auto& e : dedges[v]) {
-        B2_REQUIRE(mpo->parity[i][e.a] == 0 && mpo->parity[i + 2][e.b] == 0, B2_EINVAL,
+        B2_REQUIRE(mpo->parity[i][e.a] == 0 && mpo->parity[i + ns][e.b] == 0, B2_EINVAL,
                    "internal: odd channel on the diagonal");
         if (ka[e.a] < 0) ka[e.a] = KA++;
         if (kb[e.b] < 0) kb[e.b] = KB++;
@@ -742,15 +771,17 @@ static void build_window(b2_env_s* env, int i, WindowProgram& wp) {
   wp.comb_done = false;
 }
 
-WindowProgram& window_program(b2_env_s* env, int site) {
-  B2_REQUIRE(site >= 0 && site + 1 < env->mpo->n, B2_EINVAL, "window site out of range");
+WindowProgram& window_program(b2_env_s* env, int win) {
+  B2_REQUIRE(win >= 0 && (win & ~(kOneSite | (kOneSite - 1))) == 0, B2_EINVAL, "bad window id");
+  const int site = win_site(win), ns = win_nsite(win);
+  B2_REQUIRE(site + ns <= env->mpo->n, B2_EINVAL, "window site out of range");
   check_env(env->L[site], "L_site");
-  check_env(env->R[site + 2], "R_{site+2}");
-  auto& slot = env->windows[site];
+  check_env(env->R[site + ns], ns == 2 ? "R_{site+2}" : "R_{site+1}");
+  auto& slot = env->windows[win];
   if (!slot) slot.reset(new WindowProgram());
   WindowProgram& wp = *slot;
-  if (wp.site != site || wp.ver_l != env->L[site].version || wp.ver_r != env->R[site + 2].version)
-    build_window(env, site, wp);
+  if (wp.win != win || wp.ver_l != env->L[site].version || wp.ver_r != env->R[site + ns].version)
+    build_window(env, win, wp);
   return wp;
 }
 
@@ -839,12 +870,12 @@ void build_tc(Ctx* c, WindowProgram& wp) {
   tp.built = true;
 }
 
-BufTable window_buffers(b2_env_s* env, int site, WindowProgram& wp, const double* psi, double* out) {
+BufTable window_buffers(b2_env_s* env, WindowProgram& wp, const double* psi, double* out) {
   BufTable bt{};
   bt.p[0] = const_cast<double*>(psi);
   bt.p[1] = out;
-  bt.p[2] = env->L[site].data.as<double>();
-  bt.p[3] = env->R[site + 2].data.as<double>();
+  bt.p[2] = env->L[wp.site].data.as<double>();
+  bt.p[3] = env->R[wp.site + wp.nsite].data.as<double>();
   bt.p[4] = wp.comb_buf.as<double>();
   return bt;
 }
@@ -900,7 +931,7 @@ TcProgram& tc_program(b2_env_s* env, int site, b2_prec prec) {
     upload(c, tp.d_psi_tasks, tp.psi_tasks);
   }
   if (tp.env_prec != int(prec)) {
-    BufTable bt = window_buffers(env, site, wp, nullptr, nullptr);
+    BufTable bt = window_buffers(env, wp, nullptr, nullptr);
     ensure_comb(c, wp, bt);
     const size_t plane = size_t(std::max<int64_t>(tp.env_elems, 1)) * elem_bytes(prec);
     tp.env_planes.reset(c, 2 * plane);
@@ -917,7 +948,7 @@ void heff_apply(b2_env_s* env, int site, const double* psi, double* out, double 
                 double* flops, b2_prec prec) {
   WindowProgram& wp = window_program(env, site);
   Ctx* c = env->ctx;
-  BufTable bt = window_buffers(env, site, wp, psi, out);
+  BufTable bt = window_buffers(env, wp, psi, out);
   ensure_comb(c, wp, bt);
   TcProgram* tp = prec == B2_FP64 ? nullptr : &tc_program(env, site, prec);
   if (tp) split_psi(c, *tp, psi, prec);
@@ -959,7 +990,7 @@ void heff_apply_batched(Ctx* c, int n, b2_env_s* const* envs, const int* sites,
     const int site = sites[i];
     WindowProgram& wp = window_program(env, site);
     B2_REQUIRE(psis[i] != outs[i], B2_EINVAL, "batched H_eff: out aliases psi");
-    BufTable bt = window_buffers(env, site, wp, psis[i], outs[i]);
+    BufTable bt = window_buffers(env, wp, psis[i], outs[i]);
     ensure_comb(c, wp, bt);
     if (prec == B2_FP64) {
       groups.push_back({wp.heff.d_tasks.as<b2k::GemmTask>(), wp.heff.d_reds.as<b2k::GemmReduce>(),
@@ -1015,8 +1046,8 @@ void heff_diag(b2_env_s* env, int site, double* diag) {
     B2_CUDA(cudaMemsetAsync(work.ptr, 0, work.bytes, c->stream));
     BufTable bt{};
     bt.p[1] = wp.diag.as<double>();
-    bt.p[2] = env->L[site].data.as<double>();
-    bt.p[3] = env->R[site + 2].data.as<double>();
+    bt.p[2] = env->L[wp.site].data.as<double>();
+    bt.p[3] = env->R[wp.site + wp.nsite].data.as<double>();
     bt.p[5] = work.as<double>();
     b2k::launch_copy(int(wp.dg_copy.size()), wp.d_dg_copy.as<b2k::CopyTask>(), bt, c->stream);
     if (!wp.dg_comb.outs.empty()) wp.dg_comb.launch(c, bt);

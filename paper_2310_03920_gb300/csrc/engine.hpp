@@ -55,12 +55,24 @@ struct PsiBlock {
   int64_t off;
 };
 
-// Two-site wavefunction layout of window (i, i+1) on bonds i and i+2.
+// Window ids.  The two-site window (site, site+1) is `site`; the one-site window of `site`
+// (Sec. 2.1.2, one-site algorithm) is site | kOneSite.  A one-site window is handled as a
+// two-site window whose second site is trivial (its empty state only, identity operator):
+// its psi blocks are (jl, s, 0, jr) on bonds (site, site+1), in the order and at the offsets
+// of the site tensor's blocks (jl, s).
+constexpr int kOneSite = 1 << 24;
+inline int win_site(int win) { return win & (kOneSite - 1); }
+inline int win_nsite(int win) { return (win & kOneSite) ? 1 : 2; }
+
+// Wavefunction layout of a window on bonds i and i+nsite.  Two-site: blocks (jl, s1, s2, jr).
+// One-site: blocks (jl, s, 0, jr), or with trivial_first (jl, 0, s, jr): the same blocks at
+// the same offsets with the trivial site on the other side (the backward split reads psi
+// that way).
 struct PsiLayout {
   std::vector<PsiBlock> blocks;
   std::vector<int> lookup;   // [(jl * 4 + s1) * 4 + s2] -> block or -1
   int64_t size = 0;
-  void build(const Bond& bl, const Bond& br);
+  void build(const Bond& bl, const Bond& br, int nsite = 2, bool trivial_first = false);
   int find(int jl, int s1, int s2) const { return lookup[(size_t(jl) * 4 + s1) * 4 + s2]; }
 };
 
@@ -82,7 +94,8 @@ struct TcProgram {
 };
 
 struct WindowProgram {
-  int site = -1;
+  int win = -1;            // window id
+  int site = -1, nsite = 2;
   int ver_l = -1, ver_r = -1;
   PsiLayout psi;
   GemmProgram heff;        // bufs: 0 psi, 1 out, 2 L env, 3 R env, 4 combination buffer
@@ -124,7 +137,7 @@ struct b2_env_s {
   b2_mps_s* mps = nullptr;
   std::vector<b2::EnvBond> L, R;   // per bond
   std::map<int, std::unique_ptr<b2::WindowProgram>> windows;
-  std::map<int, b2::RhoCache> rho_cache;   // key: 2 * window + (1 for the backward split)
+  std::map<int, b2::RhoCache> rho_cache;   // key: 4 * site + 2 * (one-site) + (backward)
   int version_counter = 0;
 };
 

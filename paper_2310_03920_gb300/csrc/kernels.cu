@@ -1312,6 +1312,46 @@ void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, doub
   g_launches += 1;
 }
 
+// Krylov exponential coefficients: c = U exp(-t (Lambda - lambda_min)) U^T e_1 for the
+// k x k eigen-decomposition (evecs row-major, eigenvector j in column j; evals in any
+// order).  stats[0] = |c|^2, stats[1] = lambda_min, stats[2] = max |lambda|.  One block.
+__global__ void k_krylov_coef(int k, const double* __restrict__ evecs, const double* __restrict__ evals,
+                              double t, double* c, double* stats) {
+  __shared__ double f[64];
+  __shared__ double lmin, lmax;
+  if (threadIdx.x == 0) {
+    double a = evals[0], b = fabs(evals[0]);
+    for (int j = 1; j < k; ++j) {
+      a = fmin(a, evals[j]);
+      b = fmax(b, fabs(evals[j]));
+    }
+    lmin = a;
+    lmax = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) f[threadIdx.x] = exp(-t * (evals[threadIdx.x] - lmin)) * evecs[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(evecs[threadIdx.x * k + j], f[j], acc);
+    c[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int j = 0; j < k; ++j) s2 = fma(c[j], c[j], s2);
+    stats[0] = s2;
+    stats[1] = lmin;
+    stats[2] = lmax;
+  }
+}
+
+void launch_krylov_coef(int k, const double* evecs, const double* evals, double t, double* c,
+                        double* stats, cudaStream_t s) {
+  k_krylov_coef<<<1, 64, 0, s>>>(k, evecs, evals, t, c, stats);
+  g_launches += 1;
+}
+
 __global__ void __launch_bounds__(256) k_ritz(int k, const double* __restrict__ V,
                                               const double* __restrict__ W, int64_t ld,
                                               const double* __restrict__ sv, int sld,

@@ -215,6 +215,10 @@ void launch_select(int n, const double* vals, const int* sector, int n_sec, int 
 // out_stride).
 void launch_multidot(int k, const double* vs, int64_t ld, const double* x, int64_t n,
                      double* partial, double* out, int out_stride, cudaStream_t s);
+// c = U exp(-t (Lambda - lambda_min)) U^T e_1 of a k x k eigen-decomposition (k <= 64; evecs
+// row-major with eigenvector j in column j); stats: |c|^2, lambda_min, max |lambda|.
+void launch_krylov_coef(int k, const double* evecs, const double* evals, double t, double* c,
+                        double* stats, cudaStream_t s);
 // y = y - sum_j c[j] vs[j]   (c on device)
 void launch_multiaxpy(int k, const double* vs, int64_t ld, const double* c, double* y,
                       int64_t n, double sign, cudaStream_t s);
