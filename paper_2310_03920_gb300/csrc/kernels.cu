@@ -47,19 +47,20 @@ __device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* 
   }
 }
 
-// acc[a][b] += sum_{kk < kn} A[2 ty + a][kk] * B[kk][4 tx + b], kn rounded up to 8 (the
-// tiles are zero there, so the sums equal the full-width ones exactly)
+// acc[a][b] += sum_{kk < kn} A[ry + a][kk] * B[kk][cx + b] (ry, cx: the thread's first row
+// and column in the tile), kn rounded up to 8 (the tiles are zero there, so the sums equal
+// the full-width ones exactly)
 __device__ __forceinline__ void tile_fma(const double (*As)[kTile + 1], const double (*Bs)[kTile + 1],
-                                         int kn, int tx, int ty, double (&acc)[2][4]) {
+                                         int kn, int cx, int ry, double (&acc)[2][4]) {
   const int kn8 = (kn + 7) & ~7;
   for (int k8 = 0; k8 < kn8; k8 += 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int kk = k8 + u;
-      const double a0 = As[2 * ty][kk], a1 = As[2 * ty + 1][kk];
+      const double a0 = As[ry][kk], a1 = As[ry + 1][kk];
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const double x = Bs[kk][4 * tx + b];
+        const double x = Bs[kk][cx + b];
         acc[0][b] = fma(a0, x, acc[0][b]);
         acc[1][b] = fma(a1, x, acc[1][b]);
       }
@@ -73,10 +74,16 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
   __shared__ double Ps[kTile][kTile + 1], Xs[kTile][kTile + 1];
   __shared__ double Ts[kTile][kTile + 1], Qs[kTile][kTile + 1];
   const GemmOut o = outs[tile.out];
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r0 = tile.r0, c0 = tile.c0;
-  // a warp owns tile rows 8w .. 8w+7: warps whose rows all lie past the block only load
-  const bool live = r0 + 8 * (tid >> 5) < o.M;
+  // warp w owns the 16 x 16 quadrant (rows 16 (w >> 1), columns 16 (w & 1)) of the tile;
+  // lane l its rows ry, ry + 1 and columns cx .. cx + 3.  Warps whose quadrant lies past
+  // the block's rows or columns (or, for the intermediate, the K2 chunk) only load: the FP64
+  // pipe is the bottleneck, and padded quadrants would spend it on zeros.
+  const int qr = 16 * (warp >> 1), qc = 16 * (warp & 1);
+  const int ry = qr + 2 * (lane >> 2), cx = qc + 4 * (lane & 3);
+  const bool live_r = r0 + qr < o.M;
+  const bool live = live_r && c0 + qc < o.N;
   double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   for (int t = tile.t0; t < tile.t1; ++t) {
     const GemmTerm g = terms[t];
@@ -89,7 +96,7 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
         load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k0, tP, tid);
         load_tile(Xs, X, g.ldX, g.K1, o.N, k0, c0, tQ, tid);
         __syncthreads();
-        if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k0), tx, ty, tacc);
+        if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k0), cx, ry, tacc);
         __syncthreads();
       }
     } else {
@@ -100,17 +107,19 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
           load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k1, tP, tid);
           load_tile(Xs, X, g.ldX, g.K1, g.K2, k1, k2, false, tid);
           __syncthreads();
-          if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k1), tx, ty, tt);
+          if (live_r && qc < g.K2 - k2) tile_fma(Ps, Xs, min(kTile, g.K1 - k1), cx, ry, tt);
           __syncthreads();
         }
+        // every warp writes its quadrant of T (zeros where it skipped), so columns past the
+        // chunk are zero for the second product
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          Ts[2 * ty][4 * tx + b] = tt[0][b];
-          Ts[2 * ty + 1][4 * tx + b] = tt[1][b];
+          Ts[ry][cx + b] = tt[0][b];
+          Ts[ry + 1][cx + b] = tt[1][b];
         }
         load_tile(Qs, Q, g.ldQ, g.K2, o.N, k2, c0, tQ, tid);
         __syncthreads();
-        if (live) tile_fma(Ts, Qs, min(kTile, g.K2 - k2), tx, ty, tacc);
+        if (live) tile_fma(Ts, Qs, min(kTile, g.K2 - k2), cx, ry, tacc);
         __syncthreads();
       }
     }
@@ -124,17 +133,17 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) pt[(2 * ty + a) * kTile + 4 * tx + b] = acc[a][b];
+      for (int b = 0; b < 4; ++b) pt[(ry + a) * kTile + cx + b] = acc[a][b];
     return;
   }
   double* out = bt.p[o.buf] + o.off;
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    int r = r0 + 2 * ty + a;
+    int r = r0 + ry + a;
     if (r >= o.M) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      int c = c0 + 4 * tx + b;
+      int c = c0 + cx + b;
       if (c >= o.N) continue;
       double* p = out + int64_t(r) * o.ld + c;
       *p = o.accumulate ? *p + acc[a][b] : acc[a][b];
