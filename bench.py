@@ -721,14 +721,17 @@ def main():
     mpo_h = b2.b2_build_mpo(ctx, h, eri, 0.0, L, 0)
     mps_h = b2.b2_mps_import(ctx, bonds, sites, L, 0, center=0)
     env_h = b2.b2_env_init(ctx, mpo_h, mps_h, center=0)
-    # setup sweeps (untimed): bonds grow to M and the energy settles
+    # setup sweeps (untimed): bonds grow to M, the energy settles (1e-10) and at least four
+    # sweeps run at the full bond dimension, so that the density matrices have stopped
+    # rotating and the eigensolver's warm start is in its steady state
     settle = []
     t_settle = time.perf_counter()
-    for _ in range(14):
+    for _ in range(18):
         r = b2.b2_sweep(ctx, mpo_h, mps_h, env_h, [M], prec=prec)[0]
         settle.append(r)
-        if (r["max_bond"] >= M and len(settle) > 1
-                and abs(r["energy"] - settle[-2]["energy"]) < 1e-8):
+        at_m = sum(x["max_bond"] >= M for x in settle)
+        if (at_m >= 4 and len(settle) > 1
+                and abs(r["energy"] - settle[-2]["energy"]) < 1e-10):
             break
     t_settle = time.perf_counter() - t_settle
     # warm-up sweeps
