@@ -61,13 +61,14 @@ def parse():
                     help="window_M*: bond dimension of the n=36 window (default: from the name)")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "window_M1000", "window_M2000", "batch64", "batch64_sweeps",
-                             "grad_n24", "eig_batch"],
+                             "grad_n24", "eig_batch", "sweep_n36"],
                     help="sweep: Hubbard L=32 M=500 full sweep (default); window_M*: middle "
                          "window of the n=36 ab initio system, FP64 vs split precision; "
                          "batch64: 64 independent problems, grouped vs one-by-one launches; "
                          "grad_n24: integral gradient (1- and 2-RDM) at n=24, M=500; "
                          "eig_batch: the truncation eigensolver alone on one truncation-shaped "
-                         "batch of graded density matrices")
+                         "batch of graded density matrices; sweep_n36: full sweeps of the n=36 "
+                         "ab initio system at M = --window-m (default 1000), precision --prec")
     ap.add_argument("--batch", type=int, default=64, help="problems of the batch64 workloads")
     ap.add_argument("--sweeps", type=int, default=6, help="batch64_sweeps: sweeps per problem")
     ap.add_argument("--one-by-one", action="store_true",
@@ -593,6 +594,50 @@ def run_batch_sweeps(args):
     ctx.close()
 
 
+def run_sweep_n36(args):
+    """Full two-site sweeps (--sweeps of them) of the n = 36, N = 36 ab initio system
+    (the window leg's integrals) at bond dimension M = --window-m (default 1000) from a random
+    MPS centred at site 0 (sector recipe, seed 2), in precision --prec (split precision with
+    FP64 refinement, or FP64).  Reports per sweep: wall time, energy, products, Davidson and
+    split times, largest bond; the time includes each window's host program build."""
+    import torch
+    from paper_2310_03920_gb300 import b2
+    from synth import config_integrals, occupancies, random_mps, sector_sizes
+    h, eri, N, tsz, kind = config_integrals("abinitio_n36")
+    n = h.shape[0]
+    M = args.window_m or 1000
+    ctx = b2.Context(0)
+    t0 = time.perf_counter()
+    bonds = sector_sizes(n, N, tsz, M, occupancies(n, N, kind))
+    sites = random_mps(bonds, seed=2 + 100, center=0)
+    mpo = b2.b2_build_mpo(ctx, h, eri, 0.0, N, tsz)
+    mps = b2.b2_mps_import(ctx, bonds, sites, N, tsz, center=0)
+    env = b2.b2_env_init(ctx, mpo, mps, center=0)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    prec = b2.PRECISIONS[args.prec]
+    res = b2.b2_sweep(ctx, mpo, mps, env, [M] * max(1, args.sweeps), prec=prec)
+    sweeps = [{"seconds": r["seconds"], "energy": r["energy"], "n_matvec": r["n_matvec"],
+               "t_davidson": r["t_davidson"], "t_split": r["t_split"], "max_bond": r["max_bond"],
+               "discarded_weight": r["discarded_weight"], "matvec_flops": r["matvec_flops"]}
+              for r in res]
+    sec = sum(r["seconds"] for r in sweeps)
+    line = {"metric": METRIC, "value": sum(r["matvec_flops"] for r in sweeps) / sec / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": len(sweeps), "warmup": 0,
+            "ms_per_step": sec * 1e3 / len(sweeps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else args.prec,
+            "data": "synthetic",
+            "config": {"workload": "abinitio_n36_N36_M%d_sweep" % M, "n": n, "n_elec": N, "M": M,
+                       "start": "random MPS (sector recipe) centred at site 0"},
+            "setup_s": setup, "sweeps": sweeps,
+            "peak_device_gb": torch.cuda.max_memory_allocated() / 1e9}
+    print(json.dumps(line), flush=True)
+    b2.b2_free_env(env)
+    b2.b2_free_mps(mps)
+    b2.b2_free_mpo(mpo)
+    ctx.close()
+
+
 def run_grad(args):
     """Integral gradient dE/dh, dE/d(pq|rs) (spin-traced 1- and 2-RDM) of an n = 24,
     N = 24 ab initio MPS at M = 500 (random MPS from the sector recipe, seeded): times
@@ -703,6 +748,9 @@ def main():
         return
     if args.workload == "eig_batch":
         run_eig(args)
+        return
+    if args.workload == "sweep_n36":
+        run_sweep_n36(args)
         return
     if args.workload != "sweep":
         run_window(args)

@@ -1547,12 +1547,16 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
       }
       r.t_davidson += secs(ta, now());
     };
+    // A window's program (precombined operators, split planes) is used only until its split:
+    // the split changes one of its environments, so it is released then instead of holding
+    // device memory for every window of the chain (gigabytes per window at n = 36).
     const int last = n - ns;   // last window site
     for (int i = 0; i <= last; ++i) {
       solve(i);
       if (i < last) {
         auto ta = now();
         split_left(env, i | flag, psi, M, cutoff, &dw, &r.other_flops, nz, nr);
+        env->windows.erase(i | flag);
         r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
@@ -1562,6 +1566,7 @@ void sweep(b2_env_s* env, const b2_sweep_opts& o, b2_sweep_result* res) {
       if (i > 0) {
         auto ta = now();
         split_right(env, i | flag, psi, M, cutoff, &dw, &r.other_flops, true, nz, nr);
+        env->windows.erase(i | flag);
         r.t_split += secs(ta, now());
         r.discarded_weight = std::max(r.discarded_weight, dw);
       }
