@@ -47,6 +47,31 @@ __device__ __forceinline__ void load_tile(double (*S)[kTile + 1], const double* 
   }
 }
 
+// A tile staged through registers: fetch issues the thread's 8 global loads of a tile (the
+// elements load_tile would store), put stores them to shared memory.  Fetching the next K
+// chunk right after a barrier lets those loads run under the current chunk's FMAs.
+struct TileRegs {
+  double v[kTile * kTile / 128];
+};
+__device__ __forceinline__ void fetch_tile(TileRegs& R, const double* M, int ld, int rows, int cols,
+                                           int r0, int c0, bool trans, int tid) {
+#pragma unroll
+  for (int q = 0; q < kTile * kTile / 128; ++q) {
+    const int e = tid + 128 * q;
+    const int i = trans ? (e & 31) : (e >> 5), j = trans ? (e >> 5) : (e & 31);
+    const int r = r0 + i, c = c0 + j;
+    R.v[q] = (r < rows && c < cols) ? (trans ? M[int64_t(c) * ld + r] : M[int64_t(r) * ld + c]) : 0.0;
+  }
+}
+__device__ __forceinline__ void put_tile(double (*S)[kTile + 1], const TileRegs& R, bool trans, int tid) {
+#pragma unroll
+  for (int q = 0; q < kTile * kTile / 128; ++q) {
+    const int e = tid + 128 * q;
+    const int i = trans ? (e & 31) : (e >> 5), j = trans ? (e >> 5) : (e & 31);
+    S[i][j] = R.v[q];
+  }
+}
+
 // acc[a][b] += sum_{kk < kn} A[ry + a][kk] * B[kk][cx + b] (ry, cx: the thread's first row
 // and column in the tile), kn rounded up to 8 (the tiles are zero there, so the sums equal
 // the full-width ones exactly)
@@ -91,22 +116,37 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
     const double* X = bt.p[g.bufX] + g.offX;
     const bool tP = g.flags & kTransP, tQ = g.flags & kTransQ;
     double tacc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    TileRegs rp, rx;
     if (g.flags & kTwoOp) {
+      fetch_tile(rp, P, g.ldP, o.M, g.K1, r0, 0, tP, tid);
+      fetch_tile(rx, X, g.ldX, g.K1, o.N, 0, c0, tQ, tid);
       for (int k0 = 0; k0 < g.K1; k0 += kTile) {
-        load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k0, tP, tid);
-        load_tile(Xs, X, g.ldX, g.K1, o.N, k0, c0, tQ, tid);
+        put_tile(Ps, rp, tP, tid);
+        put_tile(Xs, rx, tQ, tid);
         __syncthreads();
+        if (k0 + kTile < g.K1) {   // next chunk in flight during this chunk's FMAs
+          fetch_tile(rp, P, g.ldP, o.M, g.K1, r0, k0 + kTile, tP, tid);
+          fetch_tile(rx, X, g.ldX, g.K1, o.N, k0 + kTile, c0, tQ, tid);
+        }
         if (live) tile_fma(Ps, Xs, min(kTile, g.K1 - k0), cx, ry, tacc);
         __syncthreads();
       }
     } else {
       const double* Q = bt.p[g.bufQ] + g.offQ;
+      fetch_tile(rp, P, g.ldP, o.M, g.K1, r0, 0, tP, tid);
+      fetch_tile(rx, X, g.ldX, g.K1, g.K2, 0, 0, false, tid);
       for (int k2 = 0; k2 < g.K2; k2 += kTile) {
         double tt[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         for (int k1 = 0; k1 < g.K1; k1 += kTile) {
-          load_tile(Ps, P, g.ldP, o.M, g.K1, r0, k1, tP, tid);
-          load_tile(Xs, X, g.ldX, g.K1, g.K2, k1, k2, false, tid);
+          put_tile(Ps, rp, tP, tid);
+          put_tile(Xs, rx, false, tid);
           __syncthreads();
+          if (k1 + kTile < g.K1) {
+            fetch_tile(rp, P, g.ldP, o.M, g.K1, r0, k1 + kTile, tP, tid);
+            fetch_tile(rx, X, g.ldX, g.K1, g.K2, k1 + kTile, k2, false, tid);
+          } else {   // X is done for this K2 chunk: its registers stage the Q chunk
+            fetch_tile(rx, Q, g.ldQ, g.K2, o.N, k2, c0, tQ, tid);
+          }
           if (live_r && qc < g.K2 - k2) tile_fma(Ps, Xs, min(kTile, g.K1 - k1), cx, ry, tt);
           __syncthreads();
         }
@@ -117,8 +157,12 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
           Ts[ry][cx + b] = tt[0][b];
           Ts[ry + 1][cx + b] = tt[1][b];
         }
-        load_tile(Qs, Q, g.ldQ, g.K2, o.N, k2, c0, tQ, tid);
+        put_tile(Qs, rx, tQ, tid);
         __syncthreads();
+        if (k2 + kTile < g.K2) {   // the next K2 chunk's first operand chunks
+          fetch_tile(rp, P, g.ldP, o.M, g.K1, r0, 0, tP, tid);
+          fetch_tile(rx, X, g.ldX, g.K1, g.K2, 0, k2 + kTile, false, tid);
+        }
         if (live) tile_fma(Ts, Qs, min(kTile, g.K2 - k2), cx, ry, tacc);
         __syncthreads();
       }
@@ -151,7 +195,7 @@ __device__ __forceinline__ void gemm_item(const GemmTask& tile, const GemmOut* _
   }
 }
 
-__global__ void __launch_bounds__(128) k_gemm(const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(128, 4) k_gemm(const GemmTask* __restrict__ tasks,
                                               const GemmOut* __restrict__ outs,
                                               const GemmTerm* __restrict__ terms, BufTable bt,
                                               double* __restrict__ partial) {
@@ -171,7 +215,7 @@ __device__ __forceinline__ int find_group(const GemmGroup* __restrict__ groups, 
   return lo;
 }
 
-__global__ void __launch_bounds__(128) k_gemm_grouped(const GemmGroup* __restrict__ groups,
+__global__ void __launch_bounds__(128, 4) k_gemm_grouped(const GemmGroup* __restrict__ groups,
                                                       int n_groups) {
   const int g = find_group(groups, n_groups, blockIdx.x, false);
   const GemmGroup& G = groups[g];
