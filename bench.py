@@ -895,9 +895,9 @@ def main():
     fp64_peak = peaks["fp64_tflops_measured"]
     # DRAM bytes per launch from ncu captures of this sweep (dram__bytes_read.sum +
     # dram__bytes_write.sum of the launches of one timed sweep): an eigensolver call = 192/61
-    # cluster launches of 0.35 MB + one one-CTA launch of 0.07 MB; k_gemm 1.32 MB (120
-    # launches, the 16 x 16 quadrant kernel)
-    traffic = {"eig": 192.0 / 61.0 * 0.35e6 + 0.07e6, "k_gemm": 1.32e6}
+    # cluster launches of 0.35 MB + one one-CTA launch of 0.07 MB; k_gemm 1.35 MB (120
+    # launches of the register-staged quadrant kernel)
+    traffic = {"eig": 192.0 / 61.0 * 0.35e6 + 0.07e6, "k_gemm": 1.35e6}
 
     def fp64_roofline(kernel, flops_, ms_, launches_, traffic_=None):
         ach = flops_ / (ms_ * 1e-3) / 1e12 if ms_ > 0 else 0.0
