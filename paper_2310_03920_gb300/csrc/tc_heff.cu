@@ -13,25 +13,28 @@
 // operators) are split once per window and reused by every Davidson product; psi is split
 // (transposed: rows = its columns m_r, K = its rows m_l) once per product.
 //
-// Contraction.  An output tile (128 rows x <= 128 columns of one psi block) receives
+// Contraction.  An output tile (64 rows x <= 64 columns of one psi block; two CTAs per SM)
+// receives
 //   sum over terms t, over 128-byte chunks c of K2 = m_r:
 //     T   = L_t[tile rows, :] psi_t[:, c]          (MMA1, FP32 in TMEM, K = m_l)
 //     T'  = split(alpha_t * T)                     (TMEM -> registers -> shared memory)
 //     acc += T' R_t[tile cols, c]^T                 (MMA2, FP32 in TMEM)
-// each product formed as hi*hi + hi*lo + lo*hi; acc is added to the FP64 output block at
-// the end (overwritten or accumulated).
+// each product formed as hi*hi + hi*lo + lo*hi; the FP32 accumulator is added to the FP64
+// output block every kGroup chain units.
 //
-// Roles (10 warps): warp 0 streams operand chunks through a byte ring of shared memory with
-// cp.async.bulk (completion on the item's mbarrier); one thread of warp 1 issues the MMAs;
-// warps 2-9 (two per TMEM lane quarter) convert T into T' and add the accumulators to the
-// output.  The MMA thread computes T of the next chain unit while the converter works on
-// the current one (two T buffers in TMEM, two T' buffers in shared memory); the sum over a
-// tile's units runs in groups of kGroup units in two TMEM accumulators, each group added to
-// the FP64 output by the converter warps while the other accumulator fills.  Every wait is bounded: a wait
-// that runs out sets the CTA's abort flag and the status word; the other roles then stop,
-// the producer waits (with the full limit) for its copies in flight, the MMA thread for its
-// MMAs, TMEM is freed and the CTA returns.  For tests of that path, stuck_polls > 0 makes
-// the MMA thread first wait that many polls on a barrier nothing arrives on.
+// Roles (6 warps): the producer warp streams operand chunks through a byte ring of shared
+// memory with cp.async.bulk (completion on the item's mbarrier) and is the only reader of
+// the term list; one thread of the MMA warp issues the MMAs; four converter warps (TMEM lane
+// quarters 0 and 1, two warps per quarter on the two column halves) convert T into T' and
+// add the accumulators to the output.  The MMA thread computes T of the next chain unit
+// while the converters work on the current one (two T buffers in TMEM, two T' buffers in
+// shared memory); the sum over a tile's units runs in groups of kGroup units in two TMEM
+// accumulators, each group added to the FP64 output by the converter warps while the other
+// accumulator fills.  Every wait is bounded: a wait that runs out sets the CTA's abort flag
+// and the status word; the other roles then stop, the producer waits (with the full limit)
+// for its copies in flight, the MMA thread for its MMAs, TMEM is freed and the CTA returns.
+// For tests of that path, stuck_polls > 0 makes the MMA thread first wait that many polls on
+// a barrier nothing arrives on.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -65,7 +68,7 @@ constexpr int kConv = 128;                           // converter threads (4 war
 constexpr int kTmemCols = 256;
 // chain units summed in one FP32 accumulator before it is added to the FP64 output: bounds
 // the FP32 rounding error of the long term sums (thousands of terms per output block)
-constexpr int kGroup = 16;
+constexpr int kGroup = 64;
 constexpr uint32_t kDefaultWait = 1u << 22;
 constexpr uint32_t kDrainWait = 1u << 22;
 
