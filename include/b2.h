@@ -223,8 +223,11 @@ typedef struct {
                                  with the averaged density matrix sum_j psi_j psi_j^T / k;
                                  each state is projected and carried to the next window.
                                  Roots beyond the first start from the unit vectors at the
-                                 smallest H_eff diagonal elements.  The MPS left at the end
-                                 carries the first root at its centre. */
+                                 smallest H_eff diagonal elements; dav_max_iter (0: 30)
+                                 bounds the products of one window's solve over all roots,
+                                 max_subspace (0: 30, at least 2 n_roots) its subspace.  The MPS left at the end
+                                 carries the first root at its centre.  Batched sweeps: one
+                                 root only (else B2_EUNSUPPORTED). */
   const double* noise;        /* host, n_sweeps entries >= 0, or NULL: weight of the
                                  perturbative noise (Sec. 2.1.6; White 2005) in each sweep's
                                  splits.  The MPO factorises exactly across the bond being
