@@ -96,12 +96,42 @@ const char* b2_last_error(b2_ctx ctx);
  *   h1   host, n_orb x n_orb row-major, h1[p*n+q] = h_pq (symmetric)
  *   eri  host, n_orb^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs)
  *   integrals with |value| <= cutoff are dropped (0 keeps every nonzero)
+ * Host work: ctx may be NULL.
  * Errors: B2_EINVAL for n_orb < 2, n_orb > 64, non-finite integrals, or (n_elec, two_sz)
  * impossible on n_orb orbitals. */
 int b2_build_mpo(b2_ctx ctx, int n_orb, const double* h1, const double* eri, double e_core,
                  int n_elec, int two_sz, double cutoff, b2_mpo* out);
 /* Number of channels on every bond (bond_dims has n_orb + 1 entries). */
 int b2_mpo_info(b2_mpo mpo, int* n_orb, int* bond_dims);
+/* Compresses the MPO's bonds (Sec. 2.3: the SVD construction, which reduces the bond
+ * dimension at a controlled error; here applied to the built exact MPO).  Host work; ctx
+ * may be NULL.  Across bond b, H = sum_w L_w (x) R_w.  The channels of the bond are grouped
+ * by the quantum numbers and parity of their left part (the identity and whole-Hamiltonian
+ * channels stay alone, so the split-precision products still take the block-Hamiltonian
+ * terms in FP64).  Per group, the Gram matrices of the complete left and right operators
+ * (trace inner products, built by recursions over the site tensors) give orthonormal bases
+ * on both sides and the group's part of H as a coefficient matrix X.  Its singular values
+ * above tol * largest are kept: the best approximation of that part in the Frobenius norm.
+ * The new channels replace the group's: new columns of the site tensor left of the bond,
+ * new rows of the one right of it.  Bonds 1..n_orb-1 are compressed in order.  tol = 0 keeps
+ * every direction of nonzero weight (removes linear dependencies only: the contracted H is
+ * unchanged to rounding).  discarded (may be NULL): the largest relative weight
+ * sqrt(dropped / total squared singular values) over the groups.  The host cost grows
+ * steeply with n (Gram recursions and Jacobi eigen-decompositions of each group: seconds at
+ * n = 16, minutes at n = 24).  A compressed MPO has no coefficient Jacobian: b2_rdm_grad
+ * returns B2_EUNSUPPORTED for it.  Errors: B2_EINVAL (tol outside [0, 1)). */
+int b2_mpo_compress(b2_ctx ctx, b2_mpo mpo, double tol, double* discarded);
+/* The MPO's tensors, host arrays: n_entries[k] (n_orb entries, always written) = entries of
+ * site k; then, for all sites in order, entry_chan (2 ints per entry: channel on bond k,
+ * channel on bond k+1) and entry_ops (16 doubles per entry: the local operator, row =
+ * output state, before the parity factor of the right channel); chan_info (3 ints per
+ * channel of bonds 0..n_orb: parity of the left part, its N and 2Sz change).  The fermion
+ * convention: the dense Hamiltonian is the contraction over sites of
+ * op_k * P^{parity of its right channel} (P = diag(+1, -1, -1, +1)), from the single channel
+ * of bond 0 to the single channel of bond n_orb.  Pointers other than n_entries may be
+ * NULL (sizes first). */
+int b2_mpo_export(b2_mpo mpo, int64_t* n_entries, int* entry_chan, double* entry_ops,
+                  int* chan_info);
 
 /* ----------------------------------------------------------------------------- MPS
  * Import a block-sparse MPS (the layout above) from host arrays.

@@ -68,6 +68,8 @@ _sig = {
     "b2_last_error": (ctypes.c_char_p, [_vp]),
     "b2_build_mpo": (_i, [_vp, _i, _vp, _vp, _d, _i, _i, _d, ctypes.POINTER(_vp)]),
     "b2_mpo_info": (_i, [_vp, ctypes.POINTER(_i), _vp]),
+    "b2_mpo_compress": (_i, [_vp, _vp, _d, ctypes.POINTER(_d)]),
+    "b2_mpo_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "b2_mps_import": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i, ctypes.POINTER(_vp)]),
     "b2_mps_size": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i)]),
     "b2_mps_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -170,12 +172,49 @@ class Context:
 
 
 def b2_build_mpo(ctx, h1, eri, e_core, n_elec, two_sz, cutoff=0.0):
+    """ctx may be None (host work)."""
     h1 = np.ascontiguousarray(h1, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
     out = _vp()
-    _check(ctx.h, lib.b2_build_mpo(ctx.h, h1.shape[0], h1.ctypes.data, eri.ctypes.data, e_core,
-                                   n_elec, two_sz, cutoff, ctypes.byref(out)))
+    h = ctx.h if ctx is not None else None
+    _check(h, lib.b2_build_mpo(h, h1.shape[0], h1.ctypes.data, eri.ctypes.data, e_core,
+                               n_elec, two_sz, cutoff, ctypes.byref(out)))
     return out
+
+
+def b2_mpo_compress(mpo, tol, ctx=None):
+    """Compresses the MPO in place; returns the largest relative discarded weight."""
+    d = _d()
+    h = ctx.h if ctx is not None else None
+    _check(h, lib.b2_mpo_compress(h, mpo, tol, ctypes.byref(d)))
+    return d.value
+
+
+def b2_mpo_export(mpo):
+    """{"bond_dims", "entries": per site a list of (w, w2, 4x4 op), "parity", "dq"}."""
+    dims = b2_mpo_info(mpo)
+    n = len(dims) - 1
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(None, lib.b2_mpo_export(mpo, cnt.ctypes.data, None, None, None))
+    tot = int(cnt.sum())
+    chan = np.zeros(2 * max(tot, 1), dtype=np.int32)
+    ops = np.zeros(16 * max(tot, 1))
+    info = np.zeros(3 * int(dims.sum()), dtype=np.int32)
+    _check(None, lib.b2_mpo_export(mpo, cnt.ctypes.data, chan.ctypes.data, ops.ctypes.data,
+                                   info.ctypes.data))
+    entries, e = [], 0
+    for k in range(n):
+        site = []
+        for _ in range(int(cnt[k])):
+            site.append((int(chan[2 * e]), int(chan[2 * e + 1]), ops[16 * e:16 * e + 16].reshape(4, 4)))
+            e += 1
+        entries.append(site)
+    parity, dq, c = [], [], 0
+    for k in range(n + 1):
+        parity.append([int(info[3 * (c + w)]) for w in range(dims[k])])
+        dq.append([(int(info[3 * (c + w) + 1]), int(info[3 * (c + w) + 2])) for w in range(dims[k])])
+        c += int(dims[k])
+    return {"bond_dims": dims, "entries": entries, "parity": parity, "dq": dq}
 
 
 def b2_mpo_info(mpo):

@@ -8,6 +8,7 @@
 
 b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e_core, int n_elec,
                             int two_sz, double cutoff);
+double mpo_compress(b2_mpo_s* mpo, double tol, std::vector<int>* dims_out);
 b2_mps_s* b2_mps_import_impl(b2::Ctx* ctx, int n, int n_elec, int two_sz, const int* n_sectors,
                              const int* sectors, const double* site_data, int center);
 void b2_mps_export_impl(b2::Ctx* ctx, b2_mps_s* mps, int* n_sectors, int* sectors,
@@ -94,9 +95,45 @@ const char* b2_last_error(b2_ctx ctx) { return ctx ? ctx->c.last_error.c_str() :
 int b2_build_mpo(b2_ctx ctx, int n_orb, const double* h1, const double* eri, double e_core,
                  int n_elec, int two_sz, double cutoff, b2_mpo* out) {
   return guarded(ctx, [&] {
-    B2_REQUIRE(ctx && h1 && eri && out, B2_EINVAL, "null argument");
+    B2_REQUIRE(h1 && eri && out, B2_EINVAL, "null argument");   // ctx may be NULL: host work
     B2_REQUIRE(std::isfinite(cutoff) && cutoff >= 0, B2_EINVAL, "cutoff must be >= 0");
     *out = b2_build_mpo_impl(n_orb, h1, eri, e_core, n_elec, two_sz, cutoff);
+  });
+}
+
+int b2_mpo_compress(b2_ctx ctx, b2_mpo mpo, double tol, double* discarded) {
+  return guarded(ctx, [&] {
+    B2_REQUIRE(mpo, B2_EINVAL, "null mpo");
+    B2_REQUIRE(std::isfinite(tol) && tol >= 0 && tol < 1, B2_EINVAL, "tol must be in [0, 1)");
+    const double d = mpo_compress(mpo, tol, nullptr);
+    if (discarded) *discarded = d;
+  });
+}
+
+int b2_mpo_export(b2_mpo mpo, int64_t* n_entries, int* entry_chan, double* entry_ops,
+                  int* chan_info) {
+  return guarded(nullptr, [&] {
+    B2_REQUIRE(mpo && n_entries, B2_EINVAL, "null argument");
+    int64_t e = 0, c = 0;
+    for (int k = 0; k < mpo->n; ++k) {
+      n_entries[k] = int64_t(mpo->W[k].size());
+      for (const auto& x : mpo->W[k]) {
+        if (entry_chan) {
+          entry_chan[2 * e] = x.w;
+          entry_chan[2 * e + 1] = x.w2;
+        }
+        if (entry_ops)
+          for (int u = 0; u < 16; ++u) entry_ops[16 * e + u] = x.m[u];
+        ++e;
+      }
+    }
+    if (chan_info)
+      for (int k = 0; k <= mpo->n; ++k)
+        for (int w = 0; w < mpo->D[k]; ++w, ++c) {
+          chan_info[3 * c] = mpo->parity[k][w];
+          chan_info[3 * c + 1] = mpo->dq[k][w].n;
+          chan_info[3 * c + 2] = mpo->dq[k][w].tsz;
+        }
   });
 }
 
@@ -403,6 +440,8 @@ int b2_sweep_batched_dims(b2_ctx ctx, int n, const b2_env* envs, const b2_sweep_
 int b2_rdm_grad(b2_ctx ctx, b2_mpo mpo, b2_mps mps, double* h1_grad, double* eri_grad) {
   return guarded(ctx, [&] {
     B2_REQUIRE(ctx && mpo && mps && h1_grad && eri_grad, B2_EINVAL, "null argument");
+    B2_REQUIRE(!mpo->compressed, B2_EUNSUPPORTED,
+               "the gradient needs the exact MPO (a compressed one has no coefficient Jacobian)");
     B2_REQUIRE(mps->ctx == &ctx->c, B2_EINVAL, "mps belongs to another context");
     ensure_device(ctx);
     b2::rdm_grad(&ctx->c, mpo, mps, h1_grad, eri_grad);

@@ -226,6 +226,7 @@ struct b2_mpo_s {
   };
   std::vector<TermRec> terms;
   std::vector<std::array<double, 16>> ops;           // local operator table
+  bool compressed = false;   // b2_mpo_compress ran: channels are combinations, no Jacobian
 };
 
 struct b2_mps_s {

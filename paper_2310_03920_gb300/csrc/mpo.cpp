@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <map>
+#include <tuple>
 
 #include "common.hpp"
 
@@ -379,4 +381,300 @@ b2_mpo_s* b2_build_mpo_impl(int n, const double* h1, const double* eri, double e
             v.end());
   }
   return mpo;
+}
+
+// ------------------------------------------------------------------ MPO compression
+namespace {
+
+// Eigen-decomposition of the symmetric n x n matrix a (row-major, overwritten) by cyclic
+// Jacobi rotations (Golub & Van Loan, sym.schur2): eigenvalues in w, eigenvectors as the
+// columns of v.  Stops when the off-diagonal mass is below 1e-30 of the matrix's.
+void host_jacobi(int n, std::vector<double>& a, std::vector<double>& w, std::vector<double>& v) {
+  v.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) v[size_t(i) * n + i] = 1.0;
+  double total = 0;
+  for (double x : a) total += x * x;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += 2 * a[size_t(p) * n + q] * a[size_t(p) * n + q];
+    if (off <= 1e-30 * total || off == 0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[size_t(p) * n + q];
+        if (apq == 0) continue;
+        const double app = a[size_t(p) * n + p], aqq = a[size_t(q) * n + q];
+        const double tau = (aqq - app) / (2 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1 + tau * tau));
+        const double c = 1 / std::sqrt(1 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+          const double akp = a[size_t(k) * n + p], akq = a[size_t(k) * n + q];
+          a[size_t(k) * n + p] = c * akp - s * akq;
+          a[size_t(k) * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+          const double apk = a[size_t(p) * n + k], aqk = a[size_t(q) * n + k];
+          a[size_t(p) * n + k] = c * apk - s * aqk;
+          a[size_t(q) * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {   // V <- V J
+          const double vkp = v[size_t(k) * n + p], vkq = v[size_t(k) * n + q];
+          v[size_t(k) * n + p] = c * vkp - s * vkq;
+          v[size_t(k) * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a[size_t(i) * n + i];
+}
+
+// A channel's incoming column (entries of W[site left of the bond] ending in it, keyed
+// (w, local element)) or outgoing row (entries of W[site right of the bond] starting in
+// it, keyed (w2, local element)), as a sparse vector.
+using Sparse = std::vector<std::pair<int64_t, double>>;
+
+}  // namespace
+
+namespace {
+
+double dot16(const double* a, const double* b) {
+  double s = 0;
+  for (int u = 0; u < 16; ++u) s += a[u] * b[u];
+  return s;
+}
+
+// Gram matrix (dense D2 x D2) of the operators a site tensor's entries build on the next
+// bond, from the Gram matrix G (D1 x D1) of the operators on the previous bond: for the
+// left parts, entries (w1 -> w2) and G of bond b-1 give G of bond b; for the right parts,
+// entries read the other way round.  Channels of different quantum numbers or parity are
+// orthogonal (their operators have zero trace products), so only pairs within one group
+// are formed; the parity factors of the fermion convention cancel within a group.
+std::vector<double> next_gram(const std::vector<b2_mpo_s::Entry>& W, bool left_to_right, int D1,
+                              const std::vector<double>& G, int D2, const std::vector<int>& group) {
+  std::vector<std::vector<const b2_mpo_s::Entry*>> by(D2);
+  for (const auto& e : W) by[left_to_right ? e.w2 : e.w].push_back(&e);
+  std::vector<double> out(size_t(D2) * D2, 0.0);
+  for (int x = 0; x < D2; ++x)
+    for (int y = x; y < D2; ++y) {
+      if (group[x] != group[y]) continue;
+      double s = 0;
+      for (const auto* e1 : by[x]) {
+        const int a1 = left_to_right ? e1->w : e1->w2;
+        for (const auto* e2 : by[y]) {
+          const int a2 = left_to_right ? e2->w : e2->w2;
+          const double g = G[size_t(a1) * D1 + a2];
+          if (g != 0) s += g * dot16(e1->m, e2->m);
+        }
+      }
+      out[size_t(x) * D2 + y] = out[size_t(y) * D2 + x] = s;
+    }
+  return out;
+}
+
+// Groups of a bond's channels: with isolate_ends, the groups that may be combined (same
+// left-part quantum numbers and parity; the identity and whole-Hamiltonian channels alone);
+// without, the classes of mutually non-orthogonal operators (same quantum numbers and
+// parity), which the Gram recursions use.
+std::vector<int> channel_groups(const b2_mpo_s* mpo, int b, int* n_groups, bool isolate_ends) {
+  std::map<std::tuple<int, int, int>, int> id;
+  std::vector<int> g(mpo->D[b]);
+  int next = 0;
+  for (int w = 0; w < mpo->D[b]; ++w) {
+    if (isolate_ends && (w == mpo->chan_I[b] || w == mpo->chan_H[b])) {
+      g[w] = next++;
+      continue;
+    }
+    auto key = std::make_tuple(mpo->dq[b][w].n, mpo->dq[b][w].tsz, mpo->parity[b][w]);
+    auto it = id.find(key);
+    if (it == id.end()) it = id.emplace(key, next++).first;
+    g[w] = it->second;
+  }
+  *n_groups = next;
+  return g;
+}
+
+}  // namespace
+
+// Bond-by-bond compression of the MPO (Sec. 2.3, the SVD construction with its controlled
+// error; see b2_mpo_compress).  H = sum_w L_w (x) R_w across bond b.  Gram matrices of the
+// complete left parts (built left to right on the current tensors) and right parts (built
+// right to left on the original ones, which the pass has not touched yet) give, per group
+// of channels, orthonormal left and right bases and the coefficient matrix X of the group's
+// part of H in them; the SVD X = Y S Z^T truncated at tol * s_max is the best approximation
+// of that part in the Frobenius norm.  New channel c: left part sum_w alpha_wc L_w, right
+// part sum_w beta_wc R_w with alpha = U_A L_A^-1/2 Y and beta = U_C L_C^-1/2 Z S (A, C the
+// group's left and right Grams), i.e. new columns of W[b-1] and rows of W[b].
+double mpo_compress(b2_mpo_s* mpo, double tol, std::vector<int>* dims_out) {
+  const int n = mpo->n;
+  // right Grams of every bond, right to left
+  std::vector<std::vector<double>> GR(n + 1);
+  GR[n] = std::vector<double>(size_t(mpo->D[n]) * mpo->D[n], 0.0);
+  for (int w = 0; w < mpo->D[n]; ++w) GR[n][size_t(w) * mpo->D[n] + w] = 1.0;
+  for (int b = n - 1; b >= 1; --b) {
+    int ng = 0;
+    std::vector<int> cls = channel_groups(mpo, b, &ng, false);
+    GR[b] = next_gram(mpo->W[b], false, mpo->D[b + 1], GR[b + 1], mpo->D[b], cls);
+  }
+  std::vector<double> GL(size_t(mpo->D[0]) * mpo->D[0], 0.0);
+  for (int w = 0; w < mpo->D[0]; ++w) GL[size_t(w) * mpo->D[0] + w] = 1.0;
+  double worst = 0;
+  const double rank_eps = 1e-13;
+  for (int b = 1; b < n; ++b) {
+    auto& Wl = mpo->W[b - 1];
+    auto& Wr = mpo->W[b];
+    const int D = mpo->D[b];
+    int ng = 0, ncls = 0;
+    std::vector<int> grp = channel_groups(mpo, b, &ng, true);
+    const std::vector<double> GLb = next_gram(Wl, true, mpo->D[b - 1], GL, D,
+                                              channel_groups(mpo, b, &ncls, false));
+    std::vector<Sparse> col(D), row(D);
+    for (const auto& e : Wl)
+      for (int u = 0; u < 16; ++u)
+        if (e.m[u] != 0) col[e.w2].push_back({int64_t(e.w) * 16 + u, e.m[u]});
+    for (const auto& e : Wr)
+      for (int u = 0; u < 16; ++u)
+        if (e.m[u] != 0) row[e.w].push_back({int64_t(e.w2) * 16 + u, e.m[u]});
+    std::vector<std::vector<int>> members(ng);
+    for (int w = 0; w < D; ++w) members[grp[w]].push_back(w);
+    std::vector<Sparse> ncol, nrow;
+    std::vector<int> npar;
+    std::vector<b2::QN> ndq;
+    int nI = -1, nH = -1;
+    // sum_x coef[x][c] vecs[mem[x]] for a coefficient matrix of m rows and ld columns
+    auto combine = [](const std::vector<Sparse>& vecs, const std::vector<int>& mem,
+                      const std::vector<double>& coef, int m, int ld, int c) {
+      std::map<int64_t, double> acc;
+      for (int x = 0; x < m; ++x) {
+        const double a = coef[size_t(x) * ld + c];
+        if (a == 0) continue;
+        for (const auto& kv : vecs[mem[x]]) acc[kv.first] += a * kv.second;
+      }
+      return Sparse(acc.begin(), acc.end());
+    };
+    for (int gi = 0; gi < ng; ++gi) {
+      const auto& mem = members[gi];
+      const int m = int(mem.size());
+      const bool special = m == 1 && (mem[0] == mpo->chan_I[b] || mem[0] == mpo->chan_H[b]);
+      if (special) {
+        if (mem[0] == mpo->chan_I[b]) nI = int(ncol.size());
+        if (mem[0] == mpo->chan_H[b]) nH = int(ncol.size());
+        ncol.push_back(col[mem[0]]);
+        nrow.push_back(row[mem[0]]);
+        npar.push_back(mpo->parity[b][mem[0]]);
+        ndq.push_back(mpo->dq[b][mem[0]]);
+        continue;
+      }
+      // the group's left and right Grams and their eigen-decompositions
+      std::vector<double> A(size_t(m) * m), C(size_t(m) * m), la, Ua, lc, Uc;
+      for (int x = 0; x < m; ++x)
+        for (int y = 0; y < m; ++y) {
+          A[size_t(x) * m + y] = GLb[size_t(mem[x]) * D + mem[y]];
+          C[size_t(x) * m + y] = GR[b][size_t(mem[x]) * D + mem[y]];
+        }
+      host_jacobi(m, A, la, Ua);
+      host_jacobi(m, C, lc, Uc);
+      double amax = 0, cmax = 0;
+      for (double v : la) amax = std::max(amax, v);
+      for (double v : lc) cmax = std::max(cmax, v);
+      std::vector<int> ka, kc;
+      for (int i = 0; i < m; ++i) {
+        if (la[i] > rank_eps * amax) ka.push_back(i);
+        if (lc[i] > rank_eps * cmax) kc.push_back(i);
+      }
+      const int ra = int(ka.size()), rc = int(kc.size());
+      if (ra == 0 || rc == 0) continue;   // the group's part of H is zero
+      // X = La^1/2 Ua^T Uc Lc^1/2 (ra x rc), its SVD through X^T X = Z S^2 Z^T
+      std::vector<double> X(size_t(ra) * rc, 0.0);
+      for (int i = 0; i < ra; ++i)
+        for (int j = 0; j < rc; ++j) {
+          double s2 = 0;
+          for (int x = 0; x < m; ++x) s2 += Ua[size_t(x) * m + ka[i]] * Uc[size_t(x) * m + kc[j]];
+          X[size_t(i) * rc + j] = std::sqrt(la[ka[i]]) * s2 * std::sqrt(lc[kc[j]]);
+        }
+      std::vector<double> XtX(size_t(rc) * rc, 0.0), s2v, Z;
+      for (int p = 0; p < rc; ++p)
+        for (int q = 0; q < rc; ++q) {
+          double v = 0;
+          for (int i = 0; i < ra; ++i) v += X[size_t(i) * rc + p] * X[size_t(i) * rc + q];
+          XtX[size_t(p) * rc + q] = v;
+        }
+      host_jacobi(rc, XtX, s2v, Z);
+      double smax2 = 0, tot = 0;
+      for (double v : s2v) {
+        smax2 = std::max(smax2, v);
+        tot += std::max(v, 0.0);
+      }
+      std::vector<int> keep;
+      double dropped = 0;
+      for (int c = 0; c < rc; ++c) {
+        if (s2v[c] > std::max(tol * tol, 1e-26) * smax2) keep.push_back(c);
+        else dropped += std::max(s2v[c], 0.0);
+      }
+      if (tot > 0) worst = std::max(worst, std::sqrt(dropped / tot));
+      const int r = int(keep.size());
+      // alpha (m x r) = Ua_k La^-1/2 Y, Y = X Z S^-1; beta (m x r) = Uc_k Lc^-1/2 Z S
+      std::vector<double> alpha(size_t(m) * std::max(r, 1), 0.0), beta(size_t(m) * std::max(r, 1), 0.0);
+      for (int c = 0; c < r; ++c) {
+        const int zc = keep[c];
+        const double sc = std::sqrt(s2v[zc]);
+        for (int i = 0; i < ra; ++i) {
+          double y = 0;   // Y[i][c]
+          for (int j = 0; j < rc; ++j) y += X[size_t(i) * rc + j] * Z[size_t(j) * rc + zc];
+          y /= sc;
+          const double f = y / std::sqrt(la[ka[i]]);
+          for (int x = 0; x < m; ++x) alpha[size_t(x) * r + c] += Ua[size_t(x) * m + ka[i]] * f;
+        }
+        for (int j = 0; j < rc; ++j) {
+          const double f = Z[size_t(j) * rc + zc] * sc / std::sqrt(lc[kc[j]]);
+          for (int x = 0; x < m; ++x) beta[size_t(x) * r + c] += Uc[size_t(x) * m + kc[j]] * f;
+        }
+      }
+      for (int c = 0; c < r; ++c) {
+        ncol.push_back(combine(col, mem, alpha, m, r, c));
+        nrow.push_back(combine(row, mem, beta, m, r, c));
+        npar.push_back(mpo->parity[b][mem[0]]);
+        ndq.push_back(mpo->dq[b][mem[0]]);
+      }
+    }
+    // rebuild W[b-1] (columns) and W[b] (rows) from the new channels
+    auto rebuild = [](const std::vector<Sparse>& vecs, bool as_col) {
+      std::map<std::pair<int, int>, std::array<double, 16>> acc;
+      for (size_t k = 0; k < vecs.size(); ++k)
+        for (const auto& kv : vecs[k]) {
+          const int other = int(kv.first / 16), u = int(kv.first % 16);
+          auto key = as_col ? std::make_pair(other, int(k)) : std::make_pair(int(k), other);
+          auto it = acc.find(key);
+          if (it == acc.end()) it = acc.emplace(key, std::array<double, 16>{}).first;
+          it->second[u] += kv.second;
+        }
+      std::vector<b2_mpo_s::Entry> out;
+      for (const auto& kv : acc) {
+        b2_mpo_s::Entry e;
+        e.w = kv.first.first;
+        e.w2 = kv.first.second;
+        bool any = false;
+        for (int u = 0; u < 16; ++u) {
+          e.m[u] = kv.second[u];
+          any |= e.m[u] != 0;
+        }
+        if (any) out.push_back(e);
+      }
+      return out;
+    };
+    Wl = rebuild(ncol, true);
+    Wr = rebuild(nrow, false);
+    mpo->D[b] = int(ncol.size());
+    mpo->parity[b] = npar;
+    mpo->dq[b] = ndq;
+    mpo->chan_I[b] = nI;
+    mpo->chan_H[b] = nH;
+    // left Gram of the new channels, for the next bond
+    int ng2 = 0;
+    GL = next_gram(Wl, true, mpo->D[b - 1], GL, mpo->D[b], channel_groups(mpo, b, &ng2, false));
+  }
+  mpo->compressed = true;
+  mpo->str_entry.clear();
+  mpo->terms.clear();
+  if (dims_out) *dims_out = mpo->D;
+  return worst;
 }
